@@ -110,24 +110,30 @@ def cosine_scores(q: np.ndarray, x: np.ndarray, a: np.ndarray | None = None,
     return s
 
 
-def _topk_rows(s: np.ndarray, cols: np.ndarray, k: int):
-    """Per row of ``s``: the k best (score desc, column asc) among ``cols``."""
+def _topk_rows(s: np.ndarray, cols: np.ndarray, k: int, exclude=None):
+    """Per row of ``s``: the k best (score desc, column asc) among ``cols``,
+    leaving out column ``exclude[r]`` for row r when given."""
     nq, n = s.shape
-    kk = min(k, n)
     idx = np.full((nq, k), -1, dtype=np.int64)
     sc = np.full((nq, k), -np.inf, dtype=np.float64)
-    if kk == 0:
-        return idx, sc
     for r in range(nq):
         row = s[r]
+        ccols = cols
+        if exclude is not None and exclude[r] >= 0:
+            keep = cols != exclude[r]
+            row, ccols = row[keep], cols[keep]
+        n = len(row)
+        kk = min(k, n)
+        if kk == 0:
+            continue
         if n > 4 * kk:
             # every row scoring at least the kk-th largest score, ties included
             t = np.partition(row, n - kk)[n - kk]
             cand = np.nonzero(row >= t)[0]
         else:
             cand = np.arange(n)
-        order = np.lexsort((cols[cand], -row[cand]))[:kk]
-        idx[r, :kk] = cols[cand[order]]
+        order = np.lexsort((ccols[cand], -row[cand]))[:kk]
+        idx[r, :kk] = ccols[cand[order]]
         sc[r, :kk] = row[cand[order]]
     return idx, sc
 
@@ -148,11 +154,13 @@ def _merge(idx_a, sc_a, idx_b, sc_b, k):
 
 
 def knn(x: np.ndarray, queries: np.ndarray, k: int, chunk: int = 65536,
-        use_blas: bool | None = None):
+        use_blas: bool | None = None, exclude=None):
     """k nearest database rows per query under cosine distance (Sec. 4).
 
-    Returns ``(idx int64[nq, k], dist float64[nq, k], score float64[nq, k])``;
-    padded slots hold -1, +inf and -inf (reading 4).
+    ``exclude[r]`` (optional) is a row that query r may not select: the
+    leave-one-out protocol of Sec. 4.2, where a kernel's own entry is not part
+    of its reference set. Returns ``(idx int64[nq, k], dist float64[nq, k],
+    score float64[nq, k])``; padded slots hold -1, +inf and -inf (reading 4).
     """
     x = np.asarray(x, dtype=np.float64)
     q = np.asarray(queries, dtype=np.float64)
@@ -167,7 +175,7 @@ def knn(x: np.ndarray, queries: np.ndarray, k: int, chunk: int = 65536,
     for lo in range(0, n, chunk):
         hi = min(n, lo + chunk)
         s = cosine_scores(q, x[lo:hi], a=a, b=norm2(x[lo:hi]), use_blas=use_blas)
-        ci, cs = _topk_rows(s, np.arange(lo, hi, dtype=np.int64), k)
+        ci, cs = _topk_rows(s, np.arange(lo, hi, dtype=np.int64), k, exclude)
         best_i, best_s = _merge(best_i, best_s, ci, cs, k)
     dist = np.where(best_i >= 0, 1.0 - best_s, np.inf)
     return best_i, dist, best_s

@@ -1,0 +1,648 @@
+// C-ABI of the feature-similarity library (declared in include/fs.h).
+//
+// Host side of the method of Sec. 4: validates arguments, owns the device
+// copy of the reference set (feature vectors and Table-1-style phase
+// orders), plans each search call into work items and candidate buffers,
+// and enqueues the kernels on the caller's stream. No call allocates device
+// memory except fs_build_db; search calls use the caller's workspace.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fs_internal.cuh"
+
+using namespace fsk;
+
+struct fs_db {
+    int dev = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    int32_t f = 0, fu = 0, fl = 0;
+    fs_precision prec = FS_FP32;
+    int32_t n_seg = 1;
+    std::vector<int64_t> seg_off;   // host copy
+    std::vector<float> r_max;       // per segment: largest row residual
+    float* raw = nullptr;
+    float* unit = nullptr;
+    double* b64 = nullptr;
+    void* lowp = nullptr;
+    float* scale = nullptr;
+    float* resid = nullptr;
+    int64_t* seq_off = nullptr;
+    int16_t* seq_ids = nullptr;
+    int64_t seq_total = 0;
+    int64_t* seg_off_dev = nullptr;
+    float* r_max_dev = nullptr;
+    uint32_t* status = nullptr;
+    unsigned long long* stats = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+fs_status fail(fs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define FS_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(FS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+void free_db(fs_db* db) {
+    if (!db) return;
+    void* ptrs[] = {db->raw, db->unit, db->b64, db->lowp, db->scale, db->resid, db->seq_off,
+                    db->seq_ids, db->seg_off_dev, db->r_max_dev, db->status, db->stats};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete db;
+}
+
+fs_status alloc(void** p, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? FS_ENOMEM : FS_ECUDA,
+                    "cudaMalloc of %zu bytes for %s failed: %s", bytes, what,
+                    cudaGetErrorString(e));
+    }
+    return FS_OK;
+}
+
+int lowp_width(int f, fs_precision prec) {
+    if (prec == FS_BF16) return (int)round_up(f, 64);
+    if (prec == FS_FP8_E4M3) return (int)round_up(f, 128);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// stage timing: CUDA events recorded on the call's stream around each stage
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    double ms[FS_NUM_STAGES] = {};
+    uint64_t calls[FS_NUM_STAGES] = {};
+    std::atomic<uint64_t> launches{0};
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+};
+
+Profiler& prof() {
+    static Profiler p;
+    return p;
+}
+
+// Records the start of a stage when timing is on; finish() records its end.
+struct StageTimer {
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(int s, cudaStream_t cs) : stage(s), st(cs) {
+        Profiler& p = prof();
+        std::lock_guard<std::mutex> g(p.mu);
+        if (!p.on) return;
+        a = p.get();
+        b = p.get();
+        if (a && b) cudaEventRecord(a, st);
+    }
+    void finish(int nlaunch) {
+        Profiler& p = prof();
+        p.launches += (uint64_t)nlaunch;
+        if (!a || !b) return;
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> g(p.mu);
+        p.pending.push_back({stage, a, b});
+        a = b = nullptr;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// error bounds of the approximate scores (see select.cu for their use)
+
+struct Bounds {
+    double scan, rq, rerank;
+};
+
+Bounds score_bounds(const fs_db* db, double r_xmax) {
+    const double u = std::ldexp(1.0, -24);
+    const int m = (int)ceil_div(db->fu, 32);
+    auto gamma = [u](double n) { return n * u / (1.0 - n * u); };
+    // |computed 1/||x|| * ||x|| - 1| <= eta: FMA sums of m squares per lane,
+    // a 5-level butterfly, a square root and a reciprocal
+    const double eta = ((m + 5) * 0.5 + 2.0) * u * 1.01;
+    // |u_q . u_x - s| for the FP32 unit vectors (each element also rounded)
+    const double th = 2.0 * u + u * u;
+    const double e_norm = (2.0 * eta + eta * eta) * (1.0 + th) + th;
+    const double U = (1.0 + eta) * (1.0 + u);   // bound on ||u||
+    Bounds b;
+    b.rerank = gamma(m + 5) * U * U + e_norm;
+    if (db->prec == FS_FP32) {
+        b.scan = gamma(db->fu) * U * U + e_norm;
+        b.rq = 0.0;
+    } else {
+        // low-precision codes c with ||u - c|| = r: |c_q.c_x - u_q.u_x| <=
+        // r_q (U + r_x) + U r_x; FP32 accumulation of exact products within
+        // 4 K u sum|p| (tensor cores may truncate); FP8 adds the two scale
+        // multiplications of the epilogue
+        const double cmax = U * (db->prec == FS_BF16 ? 1.004 : 1.1);
+        b.scan = U * r_xmax + 4.0 * db->fl * u * cmax * cmax + e_norm +
+                 (db->prec == FS_FP8_E4M3 ? 3.0 * u * cmax * cmax : 0.0);
+        b.rq = U + r_xmax;
+    }
+    b.scan = b.scan * 1.25 + 1e-12;
+    b.rq = b.rq * 1.25;
+    b.rerank = b.rerank * 1.25 + 1e-12;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// planning of one search call
+
+struct Plan {
+    std::vector<SegPlan> seg;
+    int64_t total_items = 0;
+    int64_t total_cand = 0;
+    int k_max = 0;
+    int tile_rows = 0;
+    int slots = 0;
+};
+
+struct Layout {
+    size_t plan, q_a64, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list, fb_score,
+        fb_index, total;
+};
+
+int scan_slots(const fs_db* db) { return db->num_sms * scan_fp32_ctas_per_sm(); }
+
+fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const int32_t* k,
+                    Plan& pl) {
+    const int n_seg = db->n_seg;
+    if (q_seg_off) {
+        if (q_seg_off[0] != 0 || q_seg_off[n_seg] != nq)
+            return fail(FS_EINVAL, "q_seg_off must start at 0 and end at nq=%d", nq);
+        for (int s = 0; s < n_seg; ++s)
+            if (q_seg_off[s + 1] < q_seg_off[s])
+                return fail(FS_EINVAL, "q_seg_off must be non-decreasing (segment %d)", s);
+    } else if (n_seg != 1) {
+        return fail(FS_EINVAL, "the database has %d segments: q_seg_off is required", n_seg);
+    }
+    pl.tile_rows = kFp32TileRows;
+    const int lists = kFp32Lists;
+    pl.slots = std::max(1, scan_slots(db));
+    pl.seg.resize(n_seg);
+    pl.k_max = 0;
+    int64_t work = 0;  // (query tile, row tile) pairs
+    for (int s = 0; s < n_seg; ++s) {
+        const int ks = k ? k[s] : 0;
+        if (!k || ks < 1 || ks > FS_MAX_K)
+            return fail(FS_EINVAL, "k[%d]=%d is outside 1..%d", s, ks, FS_MAX_K);
+        pl.k_max = std::max(pl.k_max, ks);
+        SegPlan& p = pl.seg[s];
+        std::memset(&p, 0, sizeof(p));
+        p.row0 = db->seg_off[s];
+        p.nrows = db->seg_off[s + 1] - db->seg_off[s];
+        p.q0 = q_seg_off ? q_seg_off[s] : 0;
+        p.nq = q_seg_off ? q_seg_off[s + 1] - q_seg_off[s] : nq;
+        p.k = ks;
+        p.qtiles = (int)ceil_div(p.nq, kQTile);
+        p.lists = lists;
+        work += (int64_t)p.qtiles * ceil_div(p.nrows, pl.tile_rows);
+    }
+    const int64_t desired = (int64_t)pl.slots * 4;
+    const int64_t tiles_per_item = std::max<int64_t>(1, ceil_div(work, desired));
+    int64_t item = 0, cand = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        SegPlan& p = pl.seg[s];
+        const int64_t row_tiles = ceil_div(p.nrows, pl.tile_rows);
+        const int64_t chunk_tiles = std::max<int64_t>(1, std::min(row_tiles, tiles_per_item));
+        p.chunk_rows = (int32_t)(chunk_tiles * pl.tile_rows);
+        p.chunks = p.nrows > 0 ? (int32_t)ceil_div(p.nrows, p.chunk_rows) : 0;
+        p.item0 = item;
+        p.cand0 = cand;
+        if (p.nq > 0 && p.nrows > 0) {
+            item += (int64_t)p.qtiles * p.chunks;
+            cand += (int64_t)p.nq * p.chunks * p.lists * kListT;
+        }
+        const Bounds b = score_bounds(db, db->r_max[s]);
+        p.bound_scan = (float)b.scan;
+        p.bound_rq = (float)b.rq;
+        p.bound_rerank = (float)b.rerank;
+    }
+    pl.total_items = item;
+    pl.total_cand = cand;
+    return FS_OK;
+}
+
+Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&off](size_t bytes) {
+        size_t at = off;
+        off += round_up((int64_t)std::max<size_t>(bytes, 1), 256);
+        return at;
+    };
+    const size_t lw = db->prec == FS_BF16 ? 2 : 1;
+    L.plan = take(sizeof(SegPlan) * pl.seg.size());
+    L.q_a64 = take(sizeof(double) * nq);
+    L.q_unit = take(sizeof(float) * (size_t)nq * db->fu);
+    L.q_lowp = take(lw * (size_t)nq * db->fl);
+    L.q_scale = take(sizeof(float) * nq);
+    L.q_resid = take(sizeof(float) * nq);
+    L.cand = take(sizeof(uint64_t) * (size_t)pl.total_cand);
+    L.counters = take(2 * sizeof(int32_t));
+    L.fb_list = take(sizeof(int32_t) * nq);
+    L.fb_score = take(sizeof(double) * (size_t)nq * kFbChunks * FS_MAX_K);
+    L.fb_index = take(sizeof(int32_t) * (size_t)nq * kFbChunks * FS_MAX_K);
+    L.total = off;
+    return L;
+}
+
+DbView db_view(const fs_db* db) {
+    DbView v;
+    v.raw = db->raw;
+    v.unit = db->unit;
+    v.b64 = db->b64;
+    v.lowp = db->lowp;
+    v.scale = db->scale;
+    v.resid = db->resid;
+    v.seq_off = db->seq_off;
+    v.seq_ids = db->seq_ids;
+    v.status = db->status;
+    v.stats = db->stats;
+    v.n = db->n;
+    v.f = db->f;
+    v.fu = db->fu;
+    v.fl = db->fl;
+    v.prec = (int32_t)db->prec;
+    return v;
+}
+
+fs_status check_device(const fs_db* db) {
+    int cur = -1;
+    FS_CUDA(cudaGetDevice(&cur));
+    if (cur != db->dev)
+        return fail(FS_EINVAL, "current device %d is not the database's device %d", cur, db->dev);
+    return FS_OK;
+}
+
+fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_seg_off,
+                 const int32_t* k, const int32_t* exclude, void* workspace, size_t ws_bytes,
+                 int32_t* idx, float* dist, int16_t* seq_out, int32_t* seq_len, int32_t l_max,
+                 int32_t* dup_of, bool gather, void* stream) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    if (nq < 0) return fail(FS_EINVAL, "nq=%d is negative", nq);
+    if (nq > 0 && (!q || !idx || !dist))
+        return fail(FS_EINVAL, "q, idx and dist must be non-NULL when nq > 0");
+    if (gather && nq > 0 && (!seq_out || !seq_len))
+        return fail(FS_EINVAL, "seq_out and seq_len must be non-NULL when nq > 0");
+    if (gather && l_max < 1) return fail(FS_EINVAL, "l_max=%d must be >= 1", l_max);
+    Plan pl;
+    fs_status st = make_plan(db, nq, q_seg_off, k, pl);
+    if (st != FS_OK) return st;
+    const Layout L = make_layout(db, nq, pl);
+    if (nq == 0) return FS_OK;
+    if (!workspace) return fail(FS_EINVAL, "workspace is NULL");
+    if (((uintptr_t)workspace & 255) != 0) return fail(FS_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(FS_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
+                    L.total);
+    st = check_device(db);
+    if (st != FS_OK) return st;
+
+    cudaStream_t cs = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    CallView c;
+    std::memset(&c, 0, sizeof(c));
+    c.plan = (const SegPlan*)(ws + L.plan);
+    c.q_raw = q;
+    c.q_a64 = (double*)(ws + L.q_a64);
+    c.q_unit = (float*)(ws + L.q_unit);
+    c.q_lowp = ws + L.q_lowp;
+    c.q_scale = (float*)(ws + L.q_scale);
+    c.q_resid = (float*)(ws + L.q_resid);
+    c.cand = (uint64_t*)(ws + L.cand);
+    c.fb_count = (int32_t*)(ws + L.counters);
+    c.work_counter = c.fb_count + 1;
+    c.fb_list = (int32_t*)(ws + L.fb_list);
+    c.fb_score = (double*)(ws + L.fb_score);
+    c.fb_index = (int32_t*)(ws + L.fb_index);
+    c.exclude = exclude;
+    c.out_idx = idx;
+    c.out_dist = dist;
+    c.nq = nq;
+    c.n_seg = db->n_seg;
+    c.k_max = pl.k_max;
+    c.total_items = pl.total_items;
+    const DbView v = db_view(db);
+
+    {
+        StageTimer t(FS_STAGE_PREPARE, cs);
+        FS_CUDA(launch_write_plan(pl.seg.data(), db->n_seg, (SegPlan*)(ws + L.plan), c.fb_count,
+                                  c.work_counter, cs));
+        FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_a64, c.q_lowp, db->fl,
+                                    c.q_scale, c.q_resid, db->prec, db->status, cs));
+        t.finish((int)ceil_div(db->n_seg, 256) + 1);
+    }
+    if (pl.total_items > 0) {
+        StageTimer t(FS_STAGE_SCAN, cs);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.total_items, pl.slots));
+        FS_CUDA(launch_scan_fp32(v, c, grid, cs));
+        t.finish(1);
+    }
+    {
+        StageTimer t(FS_STAGE_SELECT, cs);
+        FS_CUDA(launch_select(v, c, cs));
+        t.finish(1);
+    }
+    {
+        StageTimer t(FS_STAGE_FALLBACK, cs);
+        FS_CUDA(launch_fallback(v, c, db->num_sms, cs));
+        t.finish(2);
+    }
+    if (gather) {
+        StageTimer t(FS_STAGE_GATHER, cs);
+        FS_CUDA(launch_gather(v, c, seq_out, seq_len, l_max, dup_of, cs));
+        t.finish(1);
+    }
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_err.c_str(); }
+
+fs_status fs_normalize(const float* x, int64_t n, int32_t f, int64_t ld, float* x_unit,
+                       float* inv_norm, void* stream) {
+    if (n < 0) return fail(FS_EINVAL, "n=%lld is negative", (long long)n);
+    if (f < 1 || f > FS_MAX_F) return fail(FS_EINVAL, "f=%d is outside 1..%d", f, FS_MAX_F);
+    if (ld < f) return fail(FS_EINVAL, "ld=%lld is smaller than f=%d", (long long)ld, f);
+    if (n > 0 && (!x || !x_unit)) return fail(FS_EINVAL, "x and x_unit must be non-NULL");
+    FS_CUDA(launch_normalize_public(x, n, f, ld, x_unit, inv_norm, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_off,
+                      const int16_t* seq_ids, const int64_t* seg_off, int32_t n_seg,
+                      fs_precision prec, void* stream, fs_db** out) {
+    if (!out) return fail(FS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > (int64_t)INT32_MAX)
+        return fail(FS_EINVAL, "n=%lld is outside 0..2^31-1", (long long)n);
+    if (prec != FS_FP32 && prec != FS_BF16 && prec != FS_FP8_E4M3)
+        return fail(FS_EINVAL, "unknown precision %d", (int)prec);
+    const int fmax = prec == FS_FP32 ? FS_MAX_F : FS_MAX_F_TC;
+    if (f < 1 || f > fmax) return fail(FS_EINVAL, "f=%d is outside 1..%d for this precision", f, fmax);
+    if (n > 0 && (!x || !seq_off)) return fail(FS_EINVAL, "x and seq_off must be non-NULL");
+    if (!seq_off) return fail(FS_EINVAL, "seq_off must be non-NULL");
+    std::vector<int64_t> segs;
+    if (seg_off) {
+        if (n_seg < 1 || n_seg > FS_MAX_SEGMENTS)
+            return fail(FS_EINVAL, "n_seg=%d is outside 1..%d", n_seg, FS_MAX_SEGMENTS);
+        segs.assign(seg_off, seg_off + n_seg + 1);
+        if (segs[0] != 0 || segs[n_seg] != n)
+            return fail(FS_EINVAL, "seg_off must start at 0 and end at n=%lld", (long long)n);
+        for (int s = 0; s < n_seg; ++s)
+            if (segs[s + 1] < segs[s])
+                return fail(FS_EINVAL, "seg_off must be non-decreasing (segment %d)", s);
+    } else {
+        if (n_seg != 1 && n_seg != 0)
+            return fail(FS_EINVAL, "n_seg=%d given without seg_off", n_seg);
+        n_seg = 1;
+        segs = {0, n};
+    }
+
+    fs_db* db = new fs_db();
+    cudaStream_t cs = (cudaStream_t)stream;
+    fs_status st = FS_OK;
+#define FS_TRY(expr)                   \
+    do {                               \
+        st = (expr);                   \
+        if (st != FS_OK) {             \
+            free_db(db);               \
+            return st;                 \
+        }                              \
+    } while (0)
+#define FS_TRY_CUDA(call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            free_db(db);                                                                    \
+            return fail(FS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+        }                                                                                   \
+    } while (0)
+
+    FS_TRY_CUDA(cudaGetDevice(&db->dev));
+    FS_TRY_CUDA(cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->dev));
+    db->n = n;
+    db->f = f;
+    db->fu = (int)round_up(f, 32);
+    db->fl = lowp_width(f, prec);
+    db->prec = prec;
+    db->n_seg = n_seg;
+    db->seg_off = segs;
+
+    FS_TRY(alloc((void**)&db->status, sizeof(uint32_t), "status"));
+    FS_TRY(alloc((void**)&db->stats, sizeof(unsigned long long) * kNumStats, "stats"));
+    FS_TRY_CUDA(cudaMemsetAsync(db->status, 0, sizeof(uint32_t), cs));
+    FS_TRY_CUDA(cudaMemsetAsync(db->stats, 0, sizeof(unsigned long long) * kNumStats, cs));
+
+    // the phase orders: read the total length, then copy and check the CSR
+    int64_t total = 0;
+    if (n > 0) FS_TRY_CUDA(cudaMemcpyAsync(&total, seq_off + n, sizeof(int64_t),
+                                           cudaMemcpyDeviceToHost, cs));
+    FS_TRY_CUDA(cudaStreamSynchronize(cs));
+    if (total < 0 || (total > 0 && !seq_ids)) {
+        free_db(db);
+        return fail(FS_EINVAL, "seq_off[n]=%lld needs non-NULL seq_ids", (long long)total);
+    }
+    db->seq_total = total;
+    FS_TRY(alloc((void**)&db->seq_off, sizeof(int64_t) * (n + 1), "seq_off"));
+    FS_TRY(alloc((void**)&db->seq_ids, sizeof(int16_t) * std::max<int64_t>(total, 1), "seq_ids"));
+    if (n > 0) {
+        FS_TRY_CUDA(cudaMemcpyAsync(db->seq_off, seq_off, sizeof(int64_t) * (n + 1),
+                                    cudaMemcpyDeviceToDevice, cs));
+    } else {
+        FS_TRY_CUDA(cudaMemsetAsync(db->seq_off, 0, sizeof(int64_t), cs));
+    }
+    if (total > 0)
+        FS_TRY_CUDA(cudaMemcpyAsync(db->seq_ids, seq_ids, sizeof(int16_t) * total,
+                                    cudaMemcpyDeviceToDevice, cs));
+    if (n > 0) FS_TRY_CUDA(launch_check_sequences(db->seq_off, db->seq_ids, n, total, db->status, cs));
+
+    // the feature vectors
+    FS_TRY(alloc((void**)&db->raw, sizeof(float) * n * f, "raw features"));
+    FS_TRY(alloc((void**)&db->unit, sizeof(float) * n * db->fu, "unit vectors"));
+    FS_TRY(alloc((void**)&db->b64, sizeof(double) * n, "binary64 norms"));
+    FS_TRY(alloc((void**)&db->resid, sizeof(float) * n, "residuals"));
+    if (prec != FS_FP32)
+        FS_TRY(alloc(&db->lowp, (prec == FS_BF16 ? 2 : 1) * (size_t)n * db->fl, "codes"));
+    if (prec == FS_FP8_E4M3) FS_TRY(alloc((void**)&db->scale, sizeof(float) * n, "scales"));
+    if (n > 0) {
+        FS_TRY_CUDA(cudaMemcpyAsync(db->raw, x, sizeof(float) * n * f, cudaMemcpyDeviceToDevice, cs));
+        FS_TRY_CUDA(cudaMemsetAsync(db->resid, 0, sizeof(float) * n, cs));
+    }
+    FS_TRY_CUDA(launch_prepare_rows(db->raw, n, f, db->unit, db->fu, db->b64, db->lowp, db->fl,
+                                    db->scale, db->resid, prec, db->status, cs));
+
+    // per-segment largest residual (bounds of the low-precision scans)
+    FS_TRY(alloc((void**)&db->seg_off_dev, sizeof(int64_t) * (n_seg + 1), "segments"));
+    FS_TRY(alloc((void**)&db->r_max_dev, sizeof(float) * n_seg, "segment residuals"));
+    FS_TRY_CUDA(cudaMemcpyAsync(db->seg_off_dev, segs.data(), sizeof(int64_t) * (n_seg + 1),
+                                cudaMemcpyHostToDevice, cs));
+    FS_TRY_CUDA(launch_segment_max(db->resid, db->seg_off_dev, n_seg, db->r_max_dev, cs));
+    db->r_max.assign(n_seg, 0.0f);
+    FS_TRY_CUDA(cudaMemcpyAsync(db->r_max.data(), db->r_max_dev, sizeof(float) * n_seg,
+                                cudaMemcpyDeviceToHost, cs));
+    uint32_t status = 0;
+    FS_TRY_CUDA(cudaMemcpyAsync(&status, db->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
+    FS_TRY_CUDA(cudaStreamSynchronize(cs));
+    if (status & kStBadFeature) {
+        free_db(db);
+        return fail(FS_EINVAL, "a feature is non-finite or outside [2^-40, 2^50] in magnitude");
+    }
+    if (status & kStBadSequence) {
+        free_db(db);
+        return fail(FS_EINVAL, "seq_off is not a valid CSR offset array or a pass ID is negative");
+    }
+#undef FS_TRY
+#undef FS_TRY_CUDA
+    *out = db;
+    return FS_OK;
+}
+
+fs_status fs_workspace_size(const fs_db* db, int32_t nq, const int32_t* q_seg_off, size_t* bytes) {
+    if (!db || !bytes) return fail(FS_EINVAL, "db and bytes must be non-NULL");
+    if (nq < 0) return fail(FS_EINVAL, "nq=%d is negative", nq);
+    std::vector<int32_t> kk(db->n_seg, 1);
+    Plan pl;
+    fs_status st = make_plan(db, nq, q_seg_off, kk.data(), pl);
+    if (st != FS_OK) return st;
+    *bytes = make_layout(db, nq, pl).total;
+    return FS_OK;
+}
+
+fs_status fs_knn(const fs_db* db, const float* q, int32_t nq, const int32_t* q_seg_off,
+                 const int32_t* k, const int32_t* exclude, void* workspace, size_t workspace_bytes,
+                 int32_t* idx, float* dist, void* stream) {
+    return search(db, q, nq, q_seg_off, k, exclude, workspace, workspace_bytes, idx, dist, nullptr,
+                  nullptr, 0, nullptr, false, stream);
+}
+
+fs_status fs_recommend(const fs_db* db, const float* q, int32_t nq, const int32_t* q_seg_off,
+                       const int32_t* k, const int32_t* exclude, void* workspace,
+                       size_t workspace_bytes, int32_t* idx, float* dist, int16_t* seq_out,
+                       int32_t* seq_len, int32_t l_max, int32_t* dup_of, void* stream) {
+    return search(db, q, nq, q_seg_off, k, exclude, workspace, workspace_bytes, idx, dist, seq_out,
+                  seq_len, l_max, dup_of, true, stream);
+}
+
+fs_status fs_db_destroy(fs_db* db) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    cudaDeviceSynchronize();
+    free_db(db);
+    return FS_OK;
+}
+
+fs_status fs_db_check(fs_db* db, void* stream) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    cudaStream_t cs = (cudaStream_t)stream;
+    uint32_t status = 0;
+    FS_CUDA(cudaStreamSynchronize(cs));
+    FS_CUDA(cudaMemcpy(&status, db->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    FS_CUDA(cudaMemset(db->status, 0, sizeof(uint32_t)));
+    if (status & kStTimeout) return fail(FS_ETIMEOUT, "a bounded device-side wait gave up");
+    if (status & kStBadFeature)
+        return fail(FS_EINVAL, "a query feature was non-finite or out of range (treated as zero)");
+    if (status & kStOverflow) return fail(FS_ENOMEM, "an internal candidate list overflowed");
+    if (status & kStBadSequence) return fail(FS_EINVAL, "malformed phase-order CSR");
+    return FS_OK;
+}
+
+fs_status fs_profile_enable(int32_t on) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.on = on != 0;
+    return FS_OK;
+}
+
+fs_status fs_profile_read(int32_t reset, fs_profile* out) {
+    if (!out) return fail(FS_EINVAL, "out is NULL");
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    for (const auto& r : p.pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            p.ms[r.stage] += ms;
+            p.calls[r.stage] += 1;
+        }
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+    for (int i = 0; i < FS_NUM_STAGES; ++i) {
+        out->ms[i] = p.ms[i];
+        out->calls[i] = p.calls[i];
+    }
+    out->launches = p.launches.load();
+    if (reset) {
+        for (int i = 0; i < FS_NUM_STAGES; ++i) {
+            p.ms[i] = 0.0;
+            p.calls[i] = 0;
+        }
+        p.launches = 0;
+    }
+    return FS_OK;
+}
+
+fs_status fs_db_stats(fs_db* db, void* stream, int32_t reset, fs_stats* out) {
+    if (!db || !out) return fail(FS_EINVAL, "db and out must be non-NULL");
+    unsigned long long v[kNumStats];
+    FS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    FS_CUDA(cudaMemcpy(v, db->stats, sizeof(v), cudaMemcpyDeviceToHost));
+    if (reset) FS_CUDA(cudaMemset(db->stats, 0, sizeof(v)));
+    out->queries = v[kStatQueries];
+    out->certified = v[kStatCertified];
+    out->fallback = v[kStatFallback];
+    out->fp64_evals = v[kStatFp64];
+    out->near_ties = v[kStatNearTies];
+    out->rerank_evals = v[kStatRerank];
+    return FS_OK;
+}
+
+}  // extern "C"

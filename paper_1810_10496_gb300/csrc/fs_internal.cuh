@@ -1,0 +1,151 @@
+// Internal definitions shared by the kernels and the C-ABI layer.
+//
+// Ordering keys. Every candidate list orders (score, index) pairs by score
+// descending and index ascending (the tie rule of the result contract). A
+// pair is packed into one 64-bit key whose unsigned order is that order:
+// the high word is the float score mapped to an order-preserving unsigned
+// integer, the low word is (2^32 - 1 - index). Key 0 marks an empty slot
+// (it decodes to index -1 and sorts below every real score).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fs.h"
+
+namespace fsk {
+
+constexpr int kWarp = 32;
+constexpr int kListT = 16;        // entries per candidate list (>= FS_MAX_K)
+constexpr int kWindow = 64;       // candidates the rerank takes per query
+constexpr int kQTile = 128;       // queries per scan work item
+constexpr int kFbChunks = 32;     // row chunks per query in the exact fallback
+
+// device status bits (fs_db::status)
+constexpr uint32_t kStBadFeature = 1u;     // non-finite / out-of-range value
+constexpr uint32_t kStTimeout = 2u;        // a bounded wait gave up
+constexpr uint32_t kStOverflow = 4u;       // an internal list overflowed
+constexpr uint32_t kStBadSequence = 8u;    // malformed phase-order CSR
+
+// statistics slots (fs_db::stats), same order as fs_stats
+enum { kStatQueries = 0, kStatCertified, kStatFallback, kStatFp64, kStatNearTies,
+       kStatRerank, kNumStats };
+
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) {
+    return (a + b - 1) / b;
+}
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) {
+    return ceil_div(a, b) * b;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t ord_f32(float s) {
+    uint32_t u = __float_as_uint(s + 0.0f);  // -0 becomes +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f32(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+__device__ __forceinline__ uint64_t make_key(float s, uint32_t idx) {
+    return ((uint64_t)ord_f32(s) << 32) | (uint64_t)(0xffffffffu - idx);
+}
+__device__ __forceinline__ float key_score(uint64_t key) {
+    return unord_f32((uint32_t)(key >> 32));
+}
+__device__ __forceinline__ int32_t key_index(uint64_t key) {
+    return (int32_t)(0xffffffffu - (uint32_t)key);
+}
+#endif
+
+// Per-segment facts of one search call, computed on the host and written to
+// the workspace by a small kernel (so a call can be captured in a graph).
+struct SegPlan {
+    int64_t row0;        // first database row of the segment
+    int64_t nrows;       // rows in the segment
+    int64_t item0;       // first scan work item of the segment
+    int64_t cand0;       // first candidate-list entry of the segment
+    int32_t q0;          // first query of the segment
+    int32_t nq;          // queries of the segment
+    int32_t k;           // neighbours requested
+    int32_t qtiles;      // ceil(nq / kQTile)
+    int32_t chunks;      // row chunks the scan splits the segment into
+    int32_t chunk_rows;  // rows per chunk (a multiple of the scan tile)
+    int32_t lists;       // candidate lists per (query, chunk)
+    float bound_scan;    // |approximate score - exact cosine| <= bound_scan
+    float bound_rq;      //   + bound_rq * (query residual norm), per query
+    float bound_rerank;  // same bound for the FP32 rescoring of the window
+};
+static_assert(sizeof(SegPlan) == 72, "SegPlan layout");
+
+// Read-only device view of a database and of one call's workspace.
+struct DbView {
+    const float* raw;        // [n][f] features as given (binary64 scoring)
+    const float* unit;       // [n][fu] FP32 unit vectors, zero padded
+    const double* b64;       // [n] sum of squares, binary64, sequential
+    const void* lowp;        // [n][fl] BF16 or FP8 unit-vector codes
+    const float* scale;      // [n] FP8 per-vector scale (NULL for BF16)
+    const float* resid;      // [n] ||unit - dequantised||_2
+    const int64_t* seq_off;  // [n+1]
+    const int16_t* seq_ids;
+    uint32_t* status;        // device status word
+    unsigned long long* stats;
+    int64_t n;
+    int32_t f, fu, fl;
+    int32_t prec;
+};
+
+struct CallView {
+    const SegPlan* plan;      // [n_seg], in query order
+    const float* q_raw;       // [nq][f] caller's queries
+    double* q_a64;            // [nq] binary64 sum of squares of each query
+    float* q_unit;            // [nq][fu]
+    void* q_lowp;             // [nq][fl]
+    float* q_scale;           // [nq]
+    float* q_resid;           // [nq]
+    uint64_t* cand;           // candidate lists
+    int32_t* fb_count;        // queries sent to the exact fallback
+    int32_t* fb_list;         // [nq]
+    double* fb_score;         // [nq][kFbChunks][FS_MAX_K]
+    int32_t* fb_index;        // [nq][kFbChunks][FS_MAX_K]
+    int32_t* work_counter;    // dynamic scan scheduler
+    const int32_t* exclude;   // [nq] or NULL
+    int32_t* out_idx;         // [nq][k_max]
+    float* out_dist;          // [nq][k_max]
+    int32_t nq;
+    int32_t n_seg;
+    int32_t k_max;
+    int64_t total_items;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (host functions defined in the kernel translation units)
+
+// normalize.cu
+cudaError_t launch_normalize_public(const float* x, int64_t n, int f, int64_t ld,
+                                    float* x_unit, float* inv_norm, cudaStream_t st);
+cudaError_t launch_prepare_rows(const float* x, int64_t n, int f, float* unit, int fu,
+                                double* b64, void* lowp, int fl, float* scale,
+                                float* resid, int prec, uint32_t* status, cudaStream_t st);
+cudaError_t launch_check_sequences(const int64_t* off, const int16_t* ids, int64_t n,
+                                   int64_t total, uint32_t* status, cudaStream_t st);
+cudaError_t launch_segment_max(const float* v, const int64_t* seg_off_dev, int n_seg,
+                               float* out, cudaStream_t st);
+
+// select.cu
+cudaError_t launch_write_plan(const SegPlan* host_plan, int n_seg, SegPlan* dev_plan,
+                              int32_t* fb_count, int32_t* work_counter, cudaStream_t st);
+cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st);
+cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_out,
+                          int32_t* seq_len, int l_max, int32_t* dup_of, cudaStream_t st);
+
+// scan_fp32.cu
+constexpr int kFp32TileRows = 128;
+constexpr int kFp32Lists = 2;
+cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid,
+                             cudaStream_t st);
+int scan_fp32_ctas_per_sm();
+
+}  // namespace fsk

@@ -1,0 +1,209 @@
+// Row preparation: unit vectors, binary64 squared norms, BF16/FP8 codes.
+//
+// The cosine of Sec. 4.2 is the dot product of the two unit vectors, so the
+// database is stored once as x / ||x||_2 and every scan becomes a plain
+// contraction. One warp handles one row: lanes read the row with coalesced
+// loads, each lane sums the squares of its elements with FMA, the warp adds
+// the 32 partial sums in a butterfly and lane 0's total is broadcast so that
+// every element of the row is scaled by the same reciprocal norm.
+//
+// Per row the kernel also writes (when asked):
+//   - B = sum x_i^2 in binary64, summed sequentially for i = 0..F-1 without
+//     fused multiply-add (the exact-formula rescoring reuses it);
+//   - the BF16 code of each unit element (round to nearest even), or the
+//     FP8 E4M3 code of u_i / s with s = max_i |u_i| / 448 (per-vector scale);
+//   - the residual norm r = ||u - dequantised(u)||_2, which bounds how far a
+//     low-precision score can be from the FP32 one.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "fs_internal.cuh"
+
+namespace fsk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum_bcast(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return __shfl_sync(kFull, v, 0);
+}
+__device__ __forceinline__ float warp_max_bcast(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return __shfl_sync(kFull, v, 0);
+}
+
+__device__ __forceinline__ bool feature_ok(float v) {
+    float a = fabsf(v);
+    return v == 0.0f || (a >= 0x1p-40f && a <= 0x1p50f);  // also rejects NaN/inf
+}
+
+__global__ void k_normalize_public(const float* __restrict__ x, int64_t n, int f, int64_t ld,
+                                   float* __restrict__ xu, float* __restrict__ inv_out) {
+    int lane = threadIdx.x & 31;
+    int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const float* xr = x + row * ld;
+    float ss = 0.0f;
+    bool finite = true;
+    for (int i = lane; i < f; i += 32) {
+        float v = xr[i];
+        finite &= isfinite(v);
+        ss = fmaf(v, v, ss);
+    }
+    ss = warp_sum_bcast(ss);
+    finite = __all_sync(kFull, finite);
+    float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+    if (!finite) inv = __int_as_float(0x7fc00000);
+    float* ur = xu + row * (int64_t)f;
+    for (int i = lane; i < f; i += 32) ur[i] = finite ? xr[i] * inv : inv;
+    if (inv_out && lane == 0) inv_out[row] = inv;
+}
+
+// prec: FS_FP32 (no codes), FS_BF16, FS_FP8_E4M3
+__global__ void k_prepare_rows(const float* __restrict__ x, int64_t n, int f,
+                               float* __restrict__ unit, int fu, double* __restrict__ b64,
+                               void* __restrict__ lowp, int fl, float* __restrict__ scale,
+                               float* __restrict__ resid, int prec, uint32_t* status) {
+    int lane = threadIdx.x & 31;
+    int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const float* xr = x + row * (int64_t)f;
+    float ss = 0.0f, amax = 0.0f;
+    bool ok = true;
+    for (int i = lane; i < f; i += 32) {
+        float v = xr[i];
+        ok &= feature_ok(v);
+        ss = fmaf(v, v, ss);
+        amax = fmaxf(amax, fabsf(v));
+    }
+    ok = __all_sync(kFull, ok);
+    ss = warp_sum_bcast(ss);
+    amax = warp_max_bcast(amax);
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStBadFeature);
+        ss = 0.0f;  // the row is treated as all zeros
+        amax = 0.0f;
+    }
+    float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+
+    // FP32 unit vector, zero padded to fu
+    float* ur = unit + row * (int64_t)fu;
+    for (int i = lane; i < fu; i += 32) ur[i] = (ok && i < f) ? xr[i] * inv : 0.0f;
+
+    if (b64 && lane == 0) {
+        double b = 0.0;
+        if (ok) {
+            for (int i = 0; i < f; ++i) {
+                double v = (double)xr[i];
+                b = __dadd_rn(b, __dmul_rn(v, v));
+            }
+        }
+        b64[row] = b;
+    }
+
+    if (prec == FS_BF16) {
+        __nv_bfloat16* lr = reinterpret_cast<__nv_bfloat16*>(lowp) + row * (int64_t)fl;
+        float rs = 0.0f;
+        for (int i = lane; i < fl; i += 32) {
+            float u = (ok && i < f) ? xr[i] * inv : 0.0f;
+            __nv_bfloat16 c = __float2bfloat16_rn(u);
+            float e = u - __bfloat162float(c);  // exact: the rounding error of u
+            rs = fmaf(e, e, rs);
+            lr[i] = c;
+        }
+        rs = warp_sum_bcast(rs);
+        if (lane == 0) resid[row] = sqrtf(rs);
+    } else if (prec == FS_FP8_E4M3) {
+        __nv_fp8_storage_t* lr = reinterpret_cast<__nv_fp8_storage_t*>(lowp) + row * (int64_t)fl;
+        float umax = amax * inv;  // rounding is monotonic: this is max |u_i|
+        float s = umax > 0.0f ? umax / 448.0f : 0.0f;
+        float rs = 0.0f;
+        for (int i = lane; i < fl; i += 32) {
+            float u = (ok && i < f) ? xr[i] * inv : 0.0f;
+            __nv_fp8_storage_t c = 0;
+            float e = u;
+            if (s > 0.0f) {
+                c = __nv_cvt_float_to_fp8(u / s, __NV_SATFINITE, __NV_E4M3);
+                __half_raw hr = __nv_cvt_fp8_to_halfraw(c, __NV_E4M3);
+                float dq = __half2float(__half(hr));
+                // binary64 keeps s*dq exact (8 + 24 significant bits)
+                e = (float)((double)u - (double)s * (double)dq);
+            }
+            rs = fmaf(e, e, rs);
+            lr[i] = c;
+        }
+        rs = warp_sum_bcast(rs);
+        if (lane == 0) {
+            resid[row] = sqrtf(rs);
+            scale[row] = s;
+        }
+    }
+}
+
+__global__ void k_check_sequences(const int64_t* __restrict__ off, const int16_t* __restrict__ ids,
+                                  int64_t n, int64_t total, uint32_t* status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t r = t; r < n; r += stride) bad |= off[r + 1] < off[r];
+    if (t == 0) bad |= (off[0] != 0) || (off[n] != total);
+    for (int64_t i = t; i < total; i += stride) bad |= ids[i] < 0;
+    if (bad) atomicOr(status, kStBadSequence);
+}
+
+// blockIdx.y = segment; non-negative floats order like their bit patterns
+__global__ void k_segment_max(const float* __restrict__ v, const int64_t* __restrict__ seg_off,
+                              float* __restrict__ out) {
+    int s = blockIdx.y;
+    int64_t lo = seg_off[s], hi = seg_off[s + 1];
+    float m = 0.0f;
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, v[i]);
+    m = warp_max_bcast(m);
+    if ((threadIdx.x & 31) == 0 && m > 0.0f)
+        atomicMax(reinterpret_cast<int*>(out + s), __float_as_int(m));
+}
+
+}  // namespace
+
+cudaError_t launch_normalize_public(const float* x, int64_t n, int f, int64_t ld, float* x_unit,
+                                    float* inv_norm, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int warps = 8;
+    k_normalize_public<<<(unsigned)ceil_div(n, warps), warps * 32, 0, st>>>(x, n, f, ld, x_unit,
+                                                                            inv_norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_rows(const float* x, int64_t n, int f, float* unit, int fu, double* b64,
+                                void* lowp, int fl, float* scale, float* resid, int prec,
+                                uint32_t* status, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int warps = 8;
+    k_prepare_rows<<<(unsigned)ceil_div(n, warps), warps * 32, 0, st>>>(
+        x, n, f, unit, fu, b64, lowp, fl, scale, resid, prec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_sequences(const int64_t* off, const int16_t* ids, int64_t n, int64_t total,
+                                   uint32_t* status, cudaStream_t st) {
+    k_check_sequences<<<256, 256, 0, st>>>(off, ids, n, total, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_max(const float* v, const int64_t* seg_off_dev, int n_seg, float* out,
+                               cudaStream_t st) {
+    if (n_seg == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * n_seg, st);
+    if (e != cudaSuccess) return e;
+    dim3 grid(n_seg == 1 ? 512 : 8, n_seg);
+    k_segment_max<<<grid, 256, 0, st>>>(v, seg_off_dev, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fsk

@@ -1,0 +1,213 @@
+// FP32 SIMT scan: cosine scores of unit vectors with fused candidate lists.
+//
+// Sec. 4 selects, for a new kernel, the K reference kernels with the most
+// similar feature vectors under the cosine of Sec. 4.2. With unit vectors the
+// cosine is a dot product, so a block of queries against a block of database
+// rows is a small matrix product. This kernel is the plain FP32 path: a
+// register-tiled product (each thread owns 8 x 8 scores, accumulated with
+// FMA over the features in order) followed by a filter that keeps, per query
+// and per half of each row chunk, the 16 best (score, index) pairs seen.
+//
+// Work is split into items (segment, tile of 128 queries, chunk of rows);
+// persistent blocks take items from an atomic counter. Items of one row chunk
+// are numbered consecutively over the query tiles, so blocks that run at the
+// same time read the same rows and share them through L2.
+#include "fs_internal.cuh"
+
+namespace fsk {
+
+namespace {
+
+constexpr int BQ = kQTile;          // queries per item
+constexpr int BN = kFp32TileRows;   // rows per tile
+constexpr int BK = 8;               // features per pipeline step
+constexpr int THREADS = 256;
+constexpr int T = kListT;
+constexpr int SP = BN + 1;          // score-tile row pitch (odd: conflict free)
+
+struct Smem {
+    float as[2][BK][BQ];
+    float bs[2][BK][BN];
+    float s[BQ][SP];
+    uint64_t lists[T][THREADS];
+};
+
+__device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (plan[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(THREADS)
+k_scan_fp32(DbView db, CallView call) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    __shared__ int64_t s_item;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int fu = db.fu;
+
+    // list ownership in the filter: query lq, half hf of each tile's columns
+    const int lq = tid & (BQ - 1);
+    const int hf = tid >> 7;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(call.work_counter, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= call.total_items) break;
+        const int pi = find_plan(call.plan, call.n_seg, item);
+        const SegPlan p = call.plan[pi];
+        const int64_t local = item - p.item0;
+        const int chunk = (int)(local / p.qtiles);
+        const int qtile = (int)(local % p.qtiles);
+        const int qbase = p.q0 + qtile * BQ;          // first query (global)
+        const int nq_tile = min(BQ, p.nq - qtile * BQ);
+        const int64_t row_begin = p.row0 + (int64_t)chunk * p.chunk_rows;
+        const int64_t row_end = min(p.row0 + p.nrows, row_begin + p.chunk_rows);
+
+        // per-thread candidate list state
+        int cnt = 0, min_slot = 0;
+        uint64_t thr_key = 0;
+        float thr_s = -INFINITY;
+#pragma unroll
+        for (int e = 0; e < T; ++e) sm.lists[e][tid] = 0;
+        const int excl = (call.exclude && lq < nq_tile) ? call.exclude[qbase + lq] : -1;
+
+        // global-load mapping: one float4 of A and one of B per thread and step
+        const int ld_row = tid >> 1, ld_col = (tid & 1) * 4;
+        const float* qrow = call.q_unit + (int64_t)(qbase + ld_row) * fu + ld_col;
+        const bool q_ok = ld_row < nq_tile;
+
+        for (int64_t tr = row_begin; tr < row_end; tr += BN) {
+            const int64_t brow = tr + ld_row;
+            const bool b_ok = brow < row_end;
+            const float* xrow = db.unit + brow * fu + ld_col;
+
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+            float4 ra = q_ok ? *reinterpret_cast<const float4*>(qrow) : make_float4(0, 0, 0, 0);
+            float4 rb = b_ok ? __ldg(reinterpret_cast<const float4*>(xrow)) : make_float4(0, 0, 0, 0);
+            int buf = 0;
+            for (int k0 = 0; k0 < fu; k0 += BK) {
+                sm.as[buf][ld_col + 0][ld_row] = ra.x;
+                sm.as[buf][ld_col + 1][ld_row] = ra.y;
+                sm.as[buf][ld_col + 2][ld_row] = ra.z;
+                sm.as[buf][ld_col + 3][ld_row] = ra.w;
+                sm.bs[buf][ld_col + 0][ld_row] = rb.x;
+                sm.bs[buf][ld_col + 1][ld_row] = rb.y;
+                sm.bs[buf][ld_col + 2][ld_row] = rb.z;
+                sm.bs[buf][ld_col + 3][ld_row] = rb.w;
+                __syncthreads();
+                if (k0 + BK < fu) {
+                    ra = q_ok ? *reinterpret_cast<const float4*>(qrow + k0 + BK) : make_float4(0, 0, 0, 0);
+                    rb = b_ok ? __ldg(reinterpret_cast<const float4*>(xrow + k0 + BK))
+                              : make_float4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    float a[8], b[8];
+                    float4 t0 = *reinterpret_cast<const float4*>(&sm.as[buf][kk][ty * 4]);
+                    float4 t1 = *reinterpret_cast<const float4*>(&sm.as[buf][kk][64 + ty * 4]);
+                    float4 u0 = *reinterpret_cast<const float4*>(&sm.bs[buf][kk][tx * 4]);
+                    float4 u1 = *reinterpret_cast<const float4*>(&sm.bs[buf][kk][64 + tx * 4]);
+                    a[0] = t0.x; a[1] = t0.y; a[2] = t0.z; a[3] = t0.w;
+                    a[4] = t1.x; a[5] = t1.y; a[6] = t1.z; a[7] = t1.w;
+                    b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
+                    b[4] = u1.x; b[5] = u1.y; b[6] = u1.z; b[7] = u1.w;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                }
+                buf ^= 1;
+            }
+            __syncthreads();  // every thread is done with the previous score tile
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+                    sm.s[qi][rj] = acc[i][j];
+                }
+            }
+            __syncthreads();
+
+            // filter: keep this thread's 16 best of its 64 columns
+            const float* srow = &sm.s[lq][hf * 64];
+            const int64_t col_row0 = tr + hf * 64;
+            for (int j = 0; j < 64; ++j) {
+                const float sc = srow[j];
+                if (sc >= thr_s) {
+                    const int64_t row = col_row0 + j;
+                    const int32_t li = (int32_t)(row - p.row0);
+                    if (row < row_end && li != excl) {
+                        const uint64_t key = make_key(sc, (uint32_t)li);
+                        bool recompute = false;
+                        if (cnt < T) {
+                            sm.lists[cnt][tid] = key;
+                            ++cnt;
+                            recompute = (cnt == T);
+                        } else if (key > thr_key) {
+                            sm.lists[min_slot][tid] = key;
+                            recompute = true;
+                        }
+                        if (recompute) {
+                            uint64_t mn = ~0ull;
+#pragma unroll
+                            for (int e = 0; e < T; ++e) {
+                                uint64_t v = sm.lists[e][tid];
+                                if (v < mn) { mn = v; min_slot = e; }
+                            }
+                            thr_key = mn;
+                            thr_s = key_score(mn);
+                        }
+                    }
+                }
+            }
+        }
+
+        // publish this item's lists
+        if (lq < nq_tile) {
+            const int64_t qlocal = (int64_t)qtile * BQ + lq;
+            uint64_t* dst = call.cand + p.cand0 +
+                            ((qlocal * p.chunks + chunk) * p.lists + hf) * (int64_t)T;
+#pragma unroll
+            for (int e = 0; e < T; ++e) dst[e] = sm.lists[e][tid];
+        }
+        __syncthreads();  // s_item and the lists are reused by the next item
+    }
+}
+
+}  // namespace
+
+int scan_fp32_ctas_per_sm() {
+    static int cached = -1;
+    if (cached < 0) {
+        cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(Smem));
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_fp32, THREADS,
+                                                          sizeof(Smem)) != cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid, cudaStream_t st) {
+    if (call.total_items == 0) return cudaSuccess;
+    scan_fp32_ctas_per_sm();  // sets the shared-memory attribute once
+    k_scan_fp32<<<grid, THREADS, sizeof(Smem), st>>>(db, call);
+    return cudaGetLastError();
+}
+
+}  // namespace fsk

@@ -1,0 +1,498 @@
+// Selection: from the scan's candidate lists to the exact k nearest rows, and
+// the gather of their phase orders.
+//
+// Sec. 4 keeps the K reference kernels most similar to the new kernel and
+// suggests their phase orders (Table 1). The scans only approximate the
+// cosine (FP32 rounding, or BF16/FP8 codes), so this layer turns their
+// candidates into the exact binary64 ranking of the result contract:
+//
+//  1. Per query, merge the lists of every row chunk and find the k-th best
+//     approximate score t_k.
+//  2. Certify: every approximate score is within E of the true cosine. A
+//     list that filled up dropped rows scoring at most its lowest kept score
+//     tau; if tau + 2E < t_k for every full list, no dropped row can be among
+//     the k nearest. Otherwise the query goes to the exact fallback scan.
+//  3. Window: only candidates with approximate score >= t_k - 2E can be in
+//     the top k (at most 64 are taken; more also sends the query to the
+//     fallback).
+//  4. For the BF16/FP8 scans, rescore the window in FP32 from the unit
+//     vectors (bound E_r) and keep those within 2 E_r of the k-th rescored
+//     value; for the FP32 scan the scan score already is that rescoring.
+//  5. Score the survivors with the binary64 formula (sequential sums, no
+//     fused multiply-add), rank them by (score desc, index asc), write k.
+//     Survivors beyond k are the near ties the binary64 step resolves.
+#include "fs_internal.cuh"
+
+namespace fsk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPlanPerLaunch = 256;
+
+struct PlanChunk {
+    SegPlan p[kPlanPerLaunch];
+};
+
+__global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* fb_count,
+                             int32_t* work_counter) {
+    int i = threadIdx.x;
+    if (i < n) dst[i] = chunk.p[i];
+    if (i == 0 && fb_count) {
+        *fb_count = 0;
+        *work_counter = 0;
+    }
+}
+
+__device__ __forceinline__ int plan_of_query(const SegPlan* plan, int n_seg, int q) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (plan[mid].q0 <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t w = __shfl_xor_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// (s1, i1) ranks before (s2, i2): score descending, index ascending
+__device__ __forceinline__ bool better(double s1, int i1, double s2, int i2) {
+    return s1 > s2 || (s1 == s2 && i1 < i2);
+}
+
+// Warp-wide best (score, index) pair; invalid entries carry index -1 and
+// score -inf and lose to every valid one.
+__device__ __forceinline__ void warp_best(double& s, int& i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double s2 = __shfl_xor_sync(kFull, s, o);
+        int i2 = __shfl_xor_sync(kFull, i, o);
+        bool take = (i < 0) ? (i2 >= 0) : (i2 >= 0 && better(s2, i2, s, i));
+        if (take) { s = s2; i = i2; }
+    }
+}
+
+// binary64 cosine of the result contract: sums in order, no fused multiply-add
+__device__ double exact_cosine(const float* __restrict__ q, const float* __restrict__ x, int f,
+                               double a, double b) {
+    double d = 0.0;
+    for (int i = 0; i < f; ++i) d = __dadd_rn(d, __dmul_rn((double)q[i], (double)x[i]));
+    if (a == 0.0 || b == 0.0) return 0.0;
+    double s = __ddiv_rn(d, __dsqrt_rn(__dmul_rn(a, b)));
+    return s + 0.0;  // -0 becomes +0
+}
+
+__device__ __forceinline__ void write_padding(const CallView& call, int q, int from) {
+    for (int c = from + (threadIdx.x & 31); c < call.k_max; c += 32) {
+        call.out_idx[(int64_t)q * call.k_max + c] = -1;
+        call.out_dist[(int64_t)q * call.k_max + c] = INFINITY;
+    }
+}
+
+constexpr int kSelWarps = 8;
+
+struct SelShared {
+    int32_t widx[kSelWarps][kWindow];     // window rows (segment-local)
+    float wsc[kSelWarps][kWindow];        // window approximate / rescored scores
+    double w64[kSelWarps][kWindow];       // binary64 scores of the survivors
+    int32_t wsurv[kSelWarps][kWindow];    // survivor rows
+    unsigned long long stats[kNumStats];
+};
+
+__global__ void __launch_bounds__(kSelWarps * 32)
+k_select(DbView db, CallView call) {
+    __shared__ SelShared sh;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kNumStats) sh.stats[threadIdx.x] = 0;
+    __syncthreads();
+    const int q = blockIdx.x * kSelWarps + wid;
+
+    if (q < call.nq) {
+        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const int k = p.k;
+        const int64_t out0 = (int64_t)q * call.k_max;
+        const int excl = call.exclude ? call.exclude[q] : -1;
+        const double a64 = call.q_a64[q];
+        const int nrows = (int)p.nrows;
+        int nout = 0;
+
+        if (nrows == 0) {
+            nout = 0;
+        } else if (a64 == 0.0) {
+            // zero query: every cosine is 0, so the lowest indices win (d = 1)
+            int c = 0;
+            for (int r = 0; r < nrows && c < k; ++r) {
+                if (r == excl) continue;
+                if (lane == 0) {
+                    call.out_idx[out0 + c] = r;
+                    call.out_dist[out0 + c] = 1.0f;
+                }
+                ++c;
+            }
+            nout = c;
+            if (lane == 0) {
+                atomicAdd(&sh.stats[kStatQueries], 1ull);
+                atomicAdd(&sh.stats[kStatCertified], 1ull);
+            }
+        } else {
+            const int nl = p.chunks * p.lists;
+            const int64_t ne = (int64_t)nl * kListT;
+            const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * ne;
+
+            // 1. k-th best approximate key
+            uint64_t prev = ~0ull, kth = 0;
+            int ntop = 0;
+            for (int r = 0; r < k; ++r) {
+                uint64_t best = 0;
+                for (int64_t e = lane; e < ne; e += 32) {
+                    uint64_t v = cand[e];
+                    if (v < prev && v > best) best = v;
+                }
+                best = warp_max_u64(best);
+                if (best == 0) break;
+                prev = best;
+                kth = best;
+                ++ntop;
+            }
+
+            // 2. certification against the lowest kept key of every full list
+            uint64_t tau = 0;
+            for (int l = lane; l < nl; l += 32) {
+                uint64_t mn = ~0ull;
+                for (int e = 0; e < kListT; ++e) {
+                    uint64_t v = cand[(int64_t)l * kListT + e];
+                    mn = v < mn ? v : mn;
+                }
+                if (mn != 0) tau = mn > tau ? mn : tau;   // full list
+            }
+            tau = warp_max_u64(tau);
+            const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
+            const double tk = ntop ? (double)key_score(kth) : -INFINITY;
+            bool certified = (tau == 0) || ((double)key_score(tau) + 2.0 * E < tk);
+
+            // 3. window of candidates that can still reach the top k
+            int nw = 0;
+            if (certified && ntop > 0) {
+                const double lo = tk - 2.0 * E;
+                for (int64_t e0 = 0; e0 < ne; e0 += 32) {
+                    const int64_t e = e0 + lane;
+                    uint64_t v = e < ne ? cand[e] : 0;
+                    bool in = v != 0 && (double)key_score(v) >= lo;
+                    unsigned m = __ballot_sync(kFull, in);
+                    int pos = nw + __popc(m & ((1u << lane) - 1));
+                    if (in && pos < kWindow) {
+                        sh.widx[wid][pos] = key_index(v);
+                        sh.wsc[wid][pos] = key_score(v);
+                    }
+                    nw += __popc(m);
+                }
+                if (nw > kWindow) certified = false;
+            }
+            __syncwarp();
+
+            if (!certified) {
+                if (lane == 0) {
+                    int slot = atomicAdd(call.fb_count, 1);
+                    call.fb_list[slot] = q;
+                }
+                nout = -1;  // the fallback writes this query
+            } else {
+                // 4. FP32 rescoring of the window (BF16/FP8 scans)
+                double lo2 = -INFINITY;
+                if (db.prec != FS_FP32) {
+                    const float* qu = call.q_unit + (int64_t)q * db.fu;
+                    for (int w = 0; w < nw; ++w) {
+                        const float* xu = db.unit + (p.row0 + sh.widx[wid][w]) * (int64_t)db.fu;
+                        float acc = 0.0f;
+                        for (int i = lane; i < db.fu; i += 32) acc = fmaf(qu[i], xu[i], acc);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+                        acc = __shfl_sync(kFull, acc, 0);
+                        if (lane == 0) sh.wsc[wid][w] = acc;
+                    }
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(&sh.stats[kStatRerank], (unsigned long long)nw);
+                    // k-th largest rescored value
+                    // k-th largest rescored value, counting repeated values
+                    float prevv = INFINITY, kv = -INFINITY;
+                    int taken = 0;
+                    while (taken < k && taken < nw) {
+                        float m = -INFINITY;
+                        for (int w = lane; w < nw; w += 32) {
+                            float v = sh.wsc[wid][w];
+                            if (v < prevv && v > m) m = v;
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+                        int c = 0;
+                        for (int w = lane; w < nw; w += 32) c += sh.wsc[wid][w] == m;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+                        prevv = m;
+                        kv = m;
+                        taken += c;
+                    }
+                    lo2 = (double)kv - 2.0 * (double)p.bound_rerank;
+                }
+
+                // 5. binary64 scores of the survivors
+                int ns = 0;
+                for (int w0 = 0; w0 < nw; w0 += 32) {
+                    const int w = w0 + lane;
+                    bool in = w < nw && (double)sh.wsc[wid][w] >= lo2;
+                    unsigned m = __ballot_sync(kFull, in);
+                    int pos = ns + __popc(m & ((1u << lane) - 1));
+                    if (in) sh.wsurv[wid][pos] = sh.widx[wid][w];
+                    ns += __popc(m);
+                }
+                __syncwarp();
+                const float* qr = call.q_raw + (int64_t)q * db.f;
+                for (int w = lane; w < ns; w += 32) {
+                    const int64_t row = p.row0 + sh.wsurv[wid][w];
+                    sh.w64[wid][w] = exact_cosine(qr, db.raw + row * db.f, db.f, a64, db.b64[row]);
+                }
+                __syncwarp();
+                // rank by (score desc, index asc)
+                for (int w = lane; w < ns; w += 32) {
+                    const double s = sh.w64[wid][w];
+                    const int r = sh.wsurv[wid][w];
+                    int rank = 0;
+                    for (int v = 0; v < ns; ++v)
+                        rank += better(sh.w64[wid][v], sh.wsurv[wid][v], s, r);
+                    if (rank < k) {
+                        call.out_idx[out0 + rank] = r;
+                        call.out_dist[out0 + rank] = (float)(1.0 - s);
+                    }
+                }
+                nout = min(ns, k);
+                if (lane == 0) {
+                    atomicAdd(&sh.stats[kStatQueries], 1ull);
+                    atomicAdd(&sh.stats[kStatCertified], 1ull);
+                    atomicAdd(&sh.stats[kStatFp64], (unsigned long long)ns);
+                    atomicAdd(&sh.stats[kStatNearTies], (unsigned long long)(ns - nout));
+                }
+            }
+        }
+        if (nout >= 0) write_padding(call, q, nout);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumStats && sh.stats[threadIdx.x])
+        atomicAdd(&db.stats[threadIdx.x], sh.stats[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// exact fallback: binary64 scores of every row for the queries that could not
+// be certified, split into kFbChunks row chunks per query
+
+constexpr int kFbThreads = 256;
+static_assert(kFbChunks <= 32, "one lane per fallback chunk in the merge");
+
+__global__ void __launch_bounds__(kFbThreads)
+k_fallback_scan(DbView db, CallView call) {
+    __shared__ double ws[kFbThreads / 32][FS_MAX_K];
+    __shared__ int wi[kFbThreads / 32][FS_MAX_K];
+    const int nfb = *call.fb_count;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
+        const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
+        const int q = call.fb_list[slot];
+        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const int k = p.k;
+        const int excl = call.exclude ? call.exclude[q] : -1;
+        const double a64 = call.q_a64[q];
+        const int64_t per = ceil_div(p.nrows, kFbChunks);
+        const int64_t lo = chunk * per, hi = min(p.nrows, lo + per);
+        const float* qr = call.q_raw + (int64_t)q * db.f;
+
+        // per-thread best k, kept sorted
+        double ts[FS_MAX_K];
+        int ti[FS_MAX_K];
+        for (int c = 0; c < FS_MAX_K; ++c) { ts[c] = -INFINITY; ti[c] = -1; }
+        for (int64_t r = lo + threadIdx.x; r < hi; r += kFbThreads) {
+            if ((int)r == excl) continue;
+            const int64_t row = p.row0 + r;
+            const double s = exact_cosine(qr, db.raw + row * db.f, db.f, a64, db.b64[row]);
+            if (ti[k - 1] >= 0 && !better(s, (int)r, ts[k - 1], ti[k - 1])) continue;
+            int pos = k - 1;
+            while (pos > 0 && (ti[pos - 1] < 0 || better(s, (int)r, ts[pos - 1], ti[pos - 1]))) {
+                ts[pos] = ts[pos - 1];
+                ti[pos] = ti[pos - 1];
+                --pos;
+            }
+            ts[pos] = s;
+            ti[pos] = (int)r;
+        }
+        // warp merge: k rounds of warp-wide best over the lanes' list heads
+        int head = 0;
+        for (int c = 0; c < k; ++c) {
+            double s = head < k ? ts[head] : -INFINITY;
+            int i = head < k ? ti[head] : -1;
+            double bsv = s;
+            int biv = i;
+            warp_best(bsv, biv);
+            if (biv >= 0 && biv == i) ++head;
+            if (lane == 0) { ws[wid][c] = bsv; wi[wid][c] = biv; }
+        }
+        __syncthreads();
+        // block merge by warp 0 over the 8 warps' lists
+        if (wid == 0) {
+            int h = 0;  // lane < 8 owns warp lane's list
+            for (int c = 0; c < k; ++c) {
+                double s = (lane < kFbThreads / 32 && h < k) ? ws[lane][h] : -INFINITY;
+                int i = (lane < kFbThreads / 32 && h < k) ? wi[lane][h] : -1;
+                double bsv = s;
+                int biv = i;
+                warp_best(bsv, biv);
+                if (biv >= 0 && biv == i) ++h;
+                if (lane == 0) {
+                    call.fb_score[((int64_t)slot * kFbChunks + chunk) * FS_MAX_K + c] = bsv;
+                    call.fb_index[((int64_t)slot * kFbChunks + chunk) * FS_MAX_K + c] = biv;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_fallback_merge(DbView db, CallView call) {
+    __shared__ unsigned long long st[2];
+    if (threadIdx.x < 2) st[threadIdx.x] = 0;
+    __syncthreads();
+    const int nfb = *call.fb_count;
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (slot < nfb) {
+        const int q = call.fb_list[slot];
+        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const int k = p.k;
+        const int64_t out0 = (int64_t)q * call.k_max;
+        // lane c < kFbChunks owns chunk c's sorted list
+        int h = 0;
+        int nout = 0;
+        for (int c = 0; c < k; ++c) {
+            double s = -INFINITY;
+            int i = -1;
+            if (lane < kFbChunks && h < k) {
+                s = call.fb_score[((int64_t)slot * kFbChunks + lane) * FS_MAX_K + h];
+                i = call.fb_index[((int64_t)slot * kFbChunks + lane) * FS_MAX_K + h];
+            }
+            double bsv = s;
+            int biv = i;
+            warp_best(bsv, biv);
+            if (biv >= 0 && biv == i) ++h;
+            if (biv < 0) break;
+            if (lane == 0) {
+                call.out_idx[out0 + c] = biv;
+                call.out_dist[out0 + c] = (float)(1.0 - bsv);
+            }
+            ++nout;
+        }
+        write_padding(call, q, nout);
+        if (lane == 0) {
+            atomicAdd(&st[0], 1ull);
+            atomicAdd(&st[1], (unsigned long long)p.nrows);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && st[0]) {
+        atomicAdd(&db.stats[kStatQueries], st[0]);
+        atomicAdd(&db.stats[kStatFallback], st[0]);
+        atomicAdd(&db.stats[kStatFp64], st[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gather of the neighbours' phase orders: one warp per (query, slot)
+
+__global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out,
+                         int32_t* __restrict__ seq_len, int l_max, int32_t* __restrict__ dup_of) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= (int64_t)call.nq * call.k_max) return;
+    const int q = (int)(w / call.k_max), c = (int)(w % call.k_max);
+    const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+    const int r = call.out_idx[w];
+    int16_t* dst = seq_out + w * l_max;
+    int64_t lo = 0, len = 0;
+    if (r >= 0) {
+        lo = db.seq_off[p.row0 + r];
+        len = db.seq_off[p.row0 + r + 1] - lo;
+    }
+    const int64_t m = len < l_max ? len : l_max;
+    for (int i = lane; i < l_max; i += 32) dst[i] = i < m ? db.seq_ids[lo + i] : (int16_t)-1;
+    if (lane == 0) seq_len[w] = (int32_t)len;
+    if (dup_of) {
+        int first = -1;
+        if (r >= 0) {
+            for (int c2 = 0; c2 < c && first < 0; ++c2) {
+                const int r2 = call.out_idx[(int64_t)q * call.k_max + c2];
+                if (r2 < 0) continue;
+                const int64_t lo2 = db.seq_off[p.row0 + r2];
+                const int64_t len2 = db.seq_off[p.row0 + r2 + 1] - lo2;
+                if (len2 != len) continue;
+                bool same = true;
+                for (int64_t i = lane; i < len; i += 32)
+                    same &= db.seq_ids[lo + i] == db.seq_ids[lo2 + i];
+                if (__all_sync(kFull, same)) first = c2;
+            }
+        }
+        if (lane == 0) dup_of[w] = first;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_write_plan(const SegPlan* host_plan, int n_seg, SegPlan* dev_plan,
+                              int32_t* fb_count, int32_t* work_counter, cudaStream_t st) {
+    for (int base = 0; base < n_seg; base += kPlanPerLaunch) {
+        PlanChunk chunk;
+        const int n = (n_seg - base) < kPlanPerLaunch ? (n_seg - base) : kPlanPerLaunch;
+        for (int i = 0; i < n; ++i) chunk.p[i] = host_plan[base + i];
+        k_write_plan<<<1, kPlanPerLaunch, 0, st>>>(chunk, n, dev_plan + base,
+                                                   base == 0 ? fb_count : nullptr, work_counter);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st) {
+    if (call.nq == 0) return cudaSuccess;
+    k_select<<<(unsigned)ceil_div(call.nq, kSelWarps), kSelWarps * 32, 0, st>>>(db, call);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms, cudaStream_t st) {
+    if (call.nq == 0) return cudaSuccess;
+    k_fallback_scan<<<num_sms * 2, kFbThreads, 0, st>>>(db, call);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fallback_merge<<<(unsigned)ceil_div(call.nq, 8), 256, 0, st>>>(db, call);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_out, int32_t* seq_len,
+                          int l_max, int32_t* dup_of, cudaStream_t st) {
+    const int64_t warps = (int64_t)call.nq * call.k_max;
+    if (warps == 0) return cudaSuccess;
+    k_gather<<<(unsigned)ceil_div(warps, 8), 256, 0, st>>>(db, call, seq_out, seq_len, l_max,
+                                                            dup_of);
+    return cudaGetLastError();
+}
+
+}  // namespace fsk

@@ -258,6 +258,26 @@ def test_segments_are_independent():
     assert np.all(res[1][0] == -1)
 
 
+def test_leave_one_out_equals_deleting_the_row():
+    """Sec. 4.2: with a kernel as the query, only the other kernels are
+    candidates. Excluding row j must equal searching the database without
+    row j (indices above j shift by one)."""
+    w = fsgen.make("tiny_k3", n=150, q=12, f=32)
+    excl = np.array([3, -1, 0, 149, 77, 77, 5, 6, 7, 8, 9, 10])
+    i1, d1, _ = oracle.knn(w.x, w.queries, 3, exclude=excl, chunk=40)
+    for r in range(12):
+        j = excl[r]
+        if j < 0:
+            i2, d2, _ = oracle.knn(w.x, w.queries[r:r + 1], 3)
+        else:
+            i2, d2, _ = oracle.knn(np.delete(w.x, j, axis=0), w.queries[r:r + 1], 3)
+            i2 = np.where(i2 >= j, i2 + 1, i2)
+        assert np.array_equal(i1[r], i2[0]) and np.array_equal(d1[r], d2[0])
+    # a database row as its own query, left out: never returned, d > 0
+    i3, d3, _ = oracle.knn(w.x[:20], w.x[:20], 1, exclude=np.arange(20))
+    assert np.all(i3[:, 0] != np.arange(20))
+
+
 def test_gather_truncates_and_pads():
     off = np.array([0, 0, 5, 9], dtype=np.int64)
     ids = np.arange(9, dtype=np.int16)
