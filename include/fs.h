@@ -163,6 +163,35 @@ fs_status fs_recommend(const fs_db *db, const float *q, int32_t nq,
                        int16_t *seq_out, int32_t *seq_len, int32_t l_max,
                        int32_t *dup_of, void *stream);
 
+/*
+ * fs_knn_noalloc - fs_knn for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment aid. Some callers may
+ * not call cudaMalloc at all: plug-ins hosted by a framework that owns every
+ * byte of device memory, serving loops that fixed their memory at start-up
+ * and must not add to it, and latency-bound paths where an allocation's
+ * implicit device synchronisation is not acceptable. This entry point takes
+ * the same inputs and outputs as fs_knn but no workspace: its scratch is a
+ * fixed array of FS_NOALLOC_SCRATCH_BYTES in the library's own device memory,
+ * present on every GPU the library is loaded on until the process exits.
+ *   - It never allocates or frees device memory.
+ *   - A call whose scratch need (fs_workspace_size for the same nq and
+ *     q_seg_off) exceeds FS_NOALLOC_SCRATCH_BYTES returns FS_ENOMEM and
+ *     launches nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the one array, which keeps what the last
+ *     call left there; each call resets the counters it relies on and writes
+ *     every other byte before reading it. Calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race on the array: serialise
+ *     them.
+ */
+#define FS_NOALLOC_SCRATCH_BYTES (32u << 20)
+fs_status fs_knn_noalloc(const fs_db *db, const float *q, int32_t nq,
+                         const int32_t *q_seg_off, const int32_t *k,
+                         const int32_t *exclude, int32_t *idx, float *dist,
+                         void *stream);
+
 /* Frees the database's device memory (after synchronising its last use). */
 fs_status fs_db_destroy(fs_db *db);
 

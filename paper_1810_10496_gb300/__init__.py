@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfs.so")
 FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EUNSUPPORTED = range(6)
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp8_e4m3": 2}
 FS_MAX_K = 16
+FS_NOALLOC_SCRATCH_BYTES = 32 << 20
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA",
                 4: "FS_ETIMEOUT", 5: "FS_EUNSUPPORTED"}
 STAT_FIELDS = ("queries", "certified", "fallback", "fp64_evals", "near_ties", "rerank_evals")
@@ -55,6 +56,7 @@ _SIGNATURES = {
     "fs_workspace_size": [P, I32, P, ctypes.POINTER(SZ)],
     "fs_knn": [P, P, I32, P, P, P, P, SZ, P, P, P],
     "fs_recommend": [P, P, I32, P, P, P, P, SZ, P, P, P, P, I32, P, P],
+    "fs_knn_noalloc": [P, P, I32, P, P, P, P, P, P],
     "fs_db_destroy": [P],
     "fs_db_check": [P, P],
     "fs_db_stats": [P, P, I32, ctypes.POINTER(_Stats)],
@@ -227,6 +229,28 @@ def fs_knn(db: Database, q, k, q_seg_off=None, exclude=None, workspace=None, idx
     _check(lib().fs_knn(db.handle, _ptr(q), nq, _np_ptr(qs), _np_ptr(ks), _ptr(exclude),
                         _ptr(ws), ws.numel() * ws.element_size(), _ptr(idx), _ptr(dist),
                         _stream(stream)))
+    return idx, dist
+
+
+def fs_knn_noalloc(db: Database, q, k, q_seg_off=None, exclude=None, idx=None, dist=None,
+                   stream=None):
+    """fs_knn without a workspace: the scratch is the library's fixed static
+    array (FS_NOALLOC_SCRATCH_BYTES), so nothing is allocated on the device
+    for scratch. Calls that overlap on the GPU race on that array."""
+    torch = _torch()
+    q = _dev_tensor(q, torch.float32, "q")
+    nq = q.shape[0]
+    ks = _k_array(db, k)
+    qs = _host_i32(q_seg_off)
+    k_max = int(ks.max()) if len(ks) else 1
+    if idx is None:
+        idx = torch.empty((nq, k_max), device=q.device, dtype=torch.int32)
+    if dist is None:
+        dist = torch.empty((nq, k_max), device=q.device, dtype=torch.float32)
+    if exclude is not None:
+        exclude = _dev_tensor(exclude, torch.int32, "exclude")
+    _check(lib().fs_knn_noalloc(db.handle, _ptr(q), nq, _np_ptr(qs), _np_ptr(ks), _ptr(exclude),
+                                _ptr(idx), _ptr(dist), _stream(stream)))
     return idx, dist
 
 

@@ -402,6 +402,18 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
 
 }  // namespace
 
+namespace fsk {
+fs_status set_error(fs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+}  // namespace fsk
+
 extern "C" {
 
 const char* fs_last_error(void) { return g_err.c_str(); }

@@ -141,6 +141,9 @@ cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
 cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_out,
                           int32_t* seq_len, int l_max, int32_t* dup_of, cudaStream_t st);
 
+// fs_api.cu: records the message fs_last_error() returns on this thread
+fs_status set_error(fs_status st, const char* fmt, ...);
+
 // scan_fp32.cu
 constexpr int kFp32TileRows = 128;
 constexpr int kFp32Lists = 2;
