@@ -41,6 +41,8 @@ struct fs_db {
     float* r_max_dev = nullptr;
     uint32_t* status = nullptr;
     unsigned long long* stats = nullptr;
+    int64_t n_pad = 0;              // rows of the code array (tensor-core scans)
+    CUtensorMap map_x;              // TMA map of the codes (tensor-core scans)
 };
 
 namespace {
@@ -205,7 +207,11 @@ struct Layout {
         fb_index, total;
 };
 
-int scan_slots(const fs_db* db) { return db->num_sms * scan_fp32_ctas_per_sm(); }
+bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
+
+int scan_slots(const fs_db* db) {
+    return tensor_scan(db) ? db->num_sms : db->num_sms * scan_fp32_ctas_per_sm();
+}
 
 fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const int32_t* k,
                     Plan& pl) {
@@ -219,8 +225,8 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
     } else if (n_seg != 1) {
         return fail(FS_EINVAL, "the database has %d segments: q_seg_off is required", n_seg);
     }
-    pl.tile_rows = kFp32TileRows;
-    const int lists = kFp32Lists;
+    pl.tile_rows = tensor_scan(db) ? kTcTileRows : kFp32TileRows;
+    const int lists = tensor_scan(db) ? 1 : kFp32Lists;
     pl.slots = std::max(1, scan_slots(db));
     pl.seg.resize(n_seg);
     pl.k_max = 0;
@@ -278,7 +284,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.plan = take(sizeof(SegPlan) * pl.seg.size());
     L.q_a64 = take(sizeof(double) * nq);
     L.q_unit = take(sizeof(float) * (size_t)nq * db->fu);
-    L.q_lowp = take(lw * (size_t)nq * db->fl);
+    L.q_lowp = take(lw * (size_t)round_up(nq, kTcQueryRows) * db->fl);
     L.q_scale = take(sizeof(float) * nq);
     L.q_resid = take(sizeof(float) * nq);
     L.cand = take(sizeof(uint64_t) * (size_t)pl.total_cand);
@@ -379,7 +385,15 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     if (pl.total_items > 0) {
         StageTimer t(FS_STAGE_SCAN, cs);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.total_items, pl.slots));
-        FS_CUDA(launch_scan_fp32(v, c, grid, cs));
+        if (tensor_scan(db)) {
+            CUtensorMap map_q;
+            const int eb = db->prec == FS_BF16 ? 2 : 1;
+            FS_CUDA(make_code_map(&map_q, c.q_lowp, round_up(nq, kTcQueryRows), db->fl, eb,
+                                  kTcQueryRows));
+            FS_CUDA(launch_scan_tc(v, c, map_q, db->map_x, grid, cs));
+        } else {
+            FS_CUDA(launch_scan_fp32(v, c, grid, cs));
+        }
         t.finish(1);
     }
     {
@@ -521,8 +535,15 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
     FS_TRY(alloc((void**)&db->unit, sizeof(float) * n * db->fu, "unit vectors"));
     FS_TRY(alloc((void**)&db->b64, sizeof(double) * n, "binary64 norms"));
     FS_TRY(alloc((void**)&db->resid, sizeof(float) * n, "residuals"));
-    if (prec != FS_FP32)
-        FS_TRY(alloc(&db->lowp, (prec == FS_BF16 ? 2 : 1) * (size_t)n * db->fl, "codes"));
+    if (prec != FS_FP32) {
+        // whole 256-row tiles, so every TMA box lies inside the array; the
+        // padding rows stay zero
+        const int eb = prec == FS_BF16 ? 2 : 1;
+        db->n_pad = round_up(std::max<int64_t>(n, 1), kTcTileRows);
+        FS_TRY(alloc(&db->lowp, eb * (size_t)db->n_pad * db->fl, "codes"));
+        FS_TRY_CUDA(cudaMemsetAsync(db->lowp, 0, eb * (size_t)db->n_pad * db->fl, cs));
+        FS_TRY_CUDA(make_code_map(&db->map_x, db->lowp, db->n_pad, db->fl, eb, kTcTileRows));
+    }
     if (prec == FS_FP8_E4M3) FS_TRY(alloc((void**)&db->scale, sizeof(float) * n, "scales"));
     if (n > 0) {
         FS_TRY_CUDA(cudaMemcpyAsync(db->raw, x, sizeof(float) * n * f, cudaMemcpyDeviceToDevice, cs));

@@ -8,6 +8,7 @@
 // (it decodes to index -1 and sorts below every real score).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -150,5 +151,14 @@ constexpr int kFp32Lists = 2;
 cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid,
                              cudaStream_t st);
 int scan_fp32_ctas_per_sm();
+
+// scan_tc.cu (tcgen05 scan of BF16 / FP8 codes)
+constexpr int kTcTileRows = 256;
+constexpr int kTcQueryRows = 128;
+size_t scan_tc_smem_bytes();
+cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols,
+                          int elem_bytes, int box_rows);
+cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
+                           const CUtensorMap& map_x, int grid, cudaStream_t st);
 
 }  // namespace fsk

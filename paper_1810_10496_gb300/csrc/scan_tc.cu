@@ -1,0 +1,422 @@
+// Tensor-core scan (tcgen05) of BF16 or FP8 E4M3 unit vectors, with fused
+// per-query candidate lists.
+//
+// Sec. 4 picks the K reference kernels whose feature vectors are closest to
+// the new kernel's under the cosine of Sec. 4.2. Once the database rows and
+// the queries are unit vectors the scores of a block of queries against a
+// block of rows form a matrix product, which this kernel computes on the
+// 5th-generation tensor cores and filters without ever writing it out:
+//
+//   * A = 128 queries (K-major, resident in shared memory for a work item),
+//     B = 256 database rows per tile (K-major, streamed by TMA through a
+//     4-stage ring of 128-byte-swizzled K blocks), D = 128 x 256 FP32 scores
+//     in tensor memory, double buffered (2 x 256 of the 512 columns) so the
+//     epilogue of one tile overlaps the MMAs of the next.
+//   * Warp 0 issues the TMA loads, warp 1 (one thread) issues tcgen05.mma,
+//     warps 2-5 are the epilogue: thread i owns query i of the tile (TMEM
+//     lane i), reads its 256 scores with tcgen05.ld and keeps its 16 best
+//     (score, row) pairs in shared memory, tested against a running
+//     threshold with one max per 64 scores in the common case.
+//   * FP8 scores are acc * s_row * s_query (per-vector scales, Sec. 4.2's
+//     cosine of the dequantised vectors); BF16 scores are acc itself.
+//
+// Work items (query tile, row chunk) are taken in a fixed round-robin order,
+// so all roles know the sequence without talking to each other; items of one
+// chunk are numbered consecutively so concurrently running blocks share its
+// rows in L2. Every wait is bounded; a wait that gives up marks the launch
+// failed (status word), and all roles then leave their loops, wait for their
+// own outstanding copies and MMAs (bounded), free TMEM and return.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "fs_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fsk {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 192;
+constexpr int BM = 128;                     // queries per tile (MMA M)
+constexpr int BN = kTcTileRows;             // database rows per tile (MMA N)
+constexpr int kStages = 4;
+constexpr uint32_t kStageBytes = BN * 128;  // one 128-byte K block of BN rows
+constexpr uint32_t kABlockBytes = BM * 128; // one 128-byte K block of BM queries
+constexpr int kMaxKBlocks = 4;              // 256 BF16 or 512 FP8 features
+constexpr int T = kListT;
+constexpr uint32_t kTmemCols = 2 * BN;
+
+struct Bars {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tmem_full[2];
+    uint64_t tmem_empty[2];
+    uint64_t a_full;
+    uint64_t a_empty;
+    uint64_t drain;
+    uint64_t sx_ready[2];   // FP8: the tile's row scales are staged
+};
+
+__device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (plan[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Item {
+    SegPlan p;
+    int chunk, qtile, qbase, nq_tile, ntiles;
+    int64_t row_begin, row_end;
+};
+
+__device__ __forceinline__ Item decode(const CallView& call, int64_t item) {
+    Item it;
+    it.p = call.plan[find_plan(call.plan, call.n_seg, item)];
+    const int64_t local = item - it.p.item0;
+    it.chunk = (int)(local / it.p.qtiles);
+    it.qtile = (int)(local % it.p.qtiles);
+    it.qbase = it.p.q0 + it.qtile * BM;
+    it.nq_tile = min(BM, it.p.nq - it.qtile * BM);
+    it.row_begin = it.p.row0 + (int64_t)it.chunk * it.p.chunk_rows;
+    it.row_end = min(it.p.row0 + it.p.nrows, it.row_begin + it.p.chunk_rows);
+    it.ntiles = (int)ceil_div(it.row_end - it.row_begin, BN);
+    return it;
+}
+
+// Running state of one thread's candidate list (16 keys in shared memory).
+struct ListState {
+    uint64_t thr_key;  // lowest key kept once the list is full (0 before)
+    float thr_s;       // its score; -inf while the list is filling
+    int cnt;           // keys stored so far
+    int min_slot;      // slot of thr_key
+};
+
+// Offers (score, row) to the list of epilogue thread et. Out of line: it
+// runs rarely, and one copy keeps the filter loop small.
+__device__ __noinline__ ListState list_offer(ListState st, uint64_t* lists, int et, float v,
+                                             int64_t row, int64_t row_end, int64_t row0,
+                                             int excl) {
+    const int32_t li = (int32_t)(row - row0);
+    if (row >= row_end || li == excl) return st;
+    const uint64_t key = make_key(v, (uint32_t)li);
+    if (st.cnt < T) {
+        lists[st.cnt * 128 + et] = key;
+        ++st.cnt;
+        if (st.cnt < T) return st;
+    } else if (key > st.thr_key) {
+        lists[st.min_slot * 128 + et] = key;
+    } else {
+        return st;
+    }
+    uint64_t mn = ~0ull;
+    for (int e = 0; e < T; ++e) {
+        const uint64_t x = lists[e * 128 + et];
+        if (x < mn) {
+            mn = x;
+            st.min_slot = e;
+        }
+    }
+    st.thr_key = mn;
+    st.thr_s = key_score(mn);
+    return st;
+}
+
+// A bounded wait that ignores the abort flag (used to drain on the way out).
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > kWaitLimitNs) break;
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(kThreads, 1)
+k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
+          const __grid_constant__ CUtensorMap map_x, int kblocks) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ Bars bars;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+    __shared__ __align__(16) float sx[2][BN];   // FP8: the tile's row scales, per accumulator
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t a_smem = base;
+    const uint32_t b_smem = a_smem + kMaxKBlocks * kABlockBytes;
+    uint64_t* lists = reinterpret_cast<uint64_t*>(
+        smem_raw + (b_smem + kStages * kStageBytes - smem_u32(smem_raw)));
+    constexpr int kElemsPerKBlock = FP8 ? 128 : 64;
+    const uint32_t idesc = FP8 ? kIdescE4m3 : kIdescBf16;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&bars.full[s]), 1);
+            mbar_init(smem_u32(&bars.empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&bars.tmem_full[a]), 1);
+            mbar_init(smem_u32(&bars.tmem_empty[a]), 4 * 32);
+        }
+        mbar_init(smem_u32(&bars.a_full), 1);
+        mbar_init(smem_u32(&bars.a_empty), 1);
+        mbar_init(smem_u32(&bars.drain), 1);
+        mbar_init(smem_u32(&bars.sx_ready[0]), 4 * 32);
+        mbar_init(smem_u32(&bars.sx_ready[1]), 4 * 32);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            prefetch_tensormap(&map_q);
+            prefetch_tensormap(&map_x);
+            uint32_t it = 0, ic = 0, a_loads = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; ok && item < call.total_items;
+                 item += gridDim.x, ++ic) {
+                const Item w = decode(call, item);
+                ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag);
+                if (!ok) break;
+                mbar_arrive_expect_tx(smem_u32(&bars.a_full), kblocks * kABlockBytes);
+                for (int kb = 0; kb < kblocks; ++kb)
+                    tma_load_2d(a_smem + kb * kABlockBytes, &map_q, smem_u32(&bars.a_full),
+                                kb * kElemsPerKBlock, w.qbase);
+                ++a_loads;
+                for (int t = 0; ok && t < w.ntiles; ++t) {
+                    const int32_t row = (int32_t)(w.row_begin + (int64_t)t * BN);
+                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                        const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+                        ok = mbar_wait(smem_u32(&bars.empty[s]), ph ^ 1, &abort_flag);
+                        if (!ok) break;
+                        mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kStageBytes);
+                        tma_load_2d(b_smem + s * kStageBytes, &map_x, smem_u32(&bars.full[s]),
+                                    kb * kElemsPerKBlock, row);
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the block exits
+                for (uint32_t j = (it >= kStages ? it - kStages : 0); j < it; ++j)
+                    drain_wait(smem_u32(&bars.full[j % kStages]), (j / kStages) & 1);
+                if (a_loads > 0) drain_wait(smem_u32(&bars.a_full), (a_loads - 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, tcount = 0, ic = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; ok && item < call.total_items;
+                 item += gridDim.x, ++ic) {
+                const Item w = decode(call, item);
+                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                for (int t = 0; ok && t < w.ntiles; ++t, ++tcount) {
+                    const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                    ok = mbar_wait(smem_u32(&bars.tmem_empty[acc]), aph ^ 1, &abort_flag);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + acc * BN;
+                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                        const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
+                        if (!ok) break;
+                        tc_fence_after();
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad =
+                                sw128_kmajor_desc(a_smem + kb * kABlockBytes + ks * 32);
+                            const uint64_t bd =
+                                sw128_kmajor_desc(b_smem + s * kStageBytes + ks * 32);
+                            if (FP8)
+                                mma_f8(d, ad, bd, idesc, (kb | ks) != 0);
+                            else
+                                mma_f16(d, ad, bd, idesc, (kb | ks) != 0);
+                        }
+                        mma_commit(smem_u32(&bars.empty[s]));
+                    }
+                    if (ok) mma_commit(smem_u32(&bars.tmem_full[acc]));
+                }
+                if (ok) mma_commit(smem_u32(&bars.a_empty));
+            }
+            // every MMA this thread issued has finished before TMEM is freed
+            mma_commit(smem_u32(&bars.drain));
+            drain_wait(smem_u32(&bars.drain), 0);
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;              // TMEM lanes this warp may read
+        const int lq = quarter * 32 + lane;        // query row of the tile
+        const int et = threadIdx.x - 64;           // epilogue thread 0..127
+        uint32_t tcount = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; ok && item < call.total_items; item += gridDim.x) {
+            const Item w = decode(call, item);
+            const bool qvalid = lq < w.nq_tile;
+            const int excl = (call.exclude && qvalid) ? call.exclude[w.qbase + lq] : -1;
+            const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
+            ListState st;
+            st.thr_key = 0;
+            st.thr_s = -INFINITY;
+            st.cnt = 0;
+            st.min_slot = 0;
+#pragma unroll
+            for (int e = 0; e < T; ++e) lists[e * 128 + et] = 0;
+
+            for (int t = 0; t < w.ntiles; ++t, ++tcount) {
+                const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                const int64_t tile_row0 = w.row_begin + (int64_t)t * BN;
+                if (FP8) {
+                    // stage the tile's row scales (rows past the data read as 0); every
+                    // epilogue thread finished tile t-2, the last user of sx[acc], before
+                    // any thread could complete the phase of tile t-1
+                    for (int j = et; j < BN; j += 128) {
+                        const int64_t r = tile_row0 + j;
+                        sx[acc][j] = r < w.row_end ? db.scale[r] : 0.0f;
+                    }
+                    mbar_arrive(smem_u32(&bars.sx_ready[acc]));
+                    ok = mbar_wait(smem_u32(&bars.sx_ready[acc]), aph, &abort_flag);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                }
+                ok = mbar_wait(smem_u32(&bars.tmem_full[acc]), aph, &abort_flag);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 64) {
+                    uint32_t r0[32], r1[32];
+                    tmem_ld_32x32b_x32(taddr + c0, r0);
+                    tmem_ld_32x32b_x32(taddr + c0 + 32, r1);
+                    tmem_ld_wait();
+                    // FP8: w = acc * s_row here, the query scale follows (a positive
+                    // factor: the maxima below stay maxima after scaling)
+                    float v[64];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        v[j] = __uint_as_float(r0[j]);
+                        v[32 + j] = __uint_as_float(r1[j]);
+                        if (FP8) {
+                            v[j] *= sx[acc][c0 + j];
+                            v[32 + j] *= sx[acc][c0 + 32 + j];
+                        }
+                    }
+                    float gm[8];
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float a = fmaxf(fmaxf(v[8 * g], v[8 * g + 1]), fmaxf(v[8 * g + 2], v[8 * g + 3]));
+                        const float b = fmaxf(fmaxf(v[8 * g + 4], v[8 * g + 5]), fmaxf(v[8 * g + 6], v[8 * g + 7]));
+                        gm[g] = FP8 ? fmaxf(a, b) * sq : fmaxf(a, b);
+                    }
+                    const float m = fmaxf(fmaxf(fmaxf(gm[0], gm[1]), fmaxf(gm[2], gm[3])),
+                                          fmaxf(fmaxf(gm[4], gm[5]), fmaxf(gm[6], gm[7])));
+                    if (__any_sync(0xffffffffu, qvalid && m >= st.thr_s)) {
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            if (__any_sync(0xffffffffu, qvalid && gm[g] >= st.thr_s)) {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    const float sc = FP8 ? v[8 * g + i] * sq : v[8 * g + i];
+                                    if (qvalid && sc >= st.thr_s)
+                                        st = list_offer(st, lists, et, sc, tile_row0 + c0 + 8 * g + i,
+                                                        w.row_end, w.p.row0, excl);
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&bars.tmem_empty[acc]));
+            }
+            if (ok && qvalid) {
+                const int64_t qlocal = (int64_t)w.qtile * BM + lq;
+                uint64_t* dst = call.cand + w.p.cand0 + (qlocal * w.p.chunks + w.chunk) * (int64_t)T;
+#pragma unroll
+                for (int e = 0; e < T; ++e) dst[e] = lists[e * 128 + et];
+            }
+        }
+    }
+
+    if (abort_flag && threadIdx.x == 0) atomicOr(db.status, kStTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t scan_tc_smem_bytes() {
+    return 1024 + kMaxKBlocks * kABlockBytes + kStages * kStageBytes + T * 128 * sizeof(uint64_t);
+}
+
+// 2-D tensor map of a row-major [rows][cols] array of 1- or 2-byte codes,
+// boxes of (128 bytes) x box_rows, 128-byte swizzle.
+cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols, int elem_bytes,
+                          int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * elem_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                     2, const_cast<void*>(ptr), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
+                           const CUtensorMap& map_x, int grid, cudaStream_t st) {
+    if (call.total_items == 0) return cudaSuccess;
+    const bool fp8 = db.prec == FS_FP8_E4M3;
+    const int kblocks = (int)(db.fl * (fp8 ? 1 : 2) / 128);
+    if (kblocks < 1 || kblocks > kMaxKBlocks) return cudaErrorInvalidValue;
+    const size_t smem = scan_tc_smem_bytes();
+    static bool attr_set[2] = {false, false};
+    if (fp8) {
+        if (!attr_set[1]) {
+            cudaFuncSetAttribute(k_scan_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set[1] = true;
+        }
+        k_scan_tc<true><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
+    } else {
+        if (!attr_set[0]) {
+            cudaFuncSetAttribute(k_scan_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set[0] = true;
+        }
+        k_scan_tc<false><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fsk
