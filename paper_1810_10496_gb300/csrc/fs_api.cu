@@ -200,11 +200,12 @@ struct Plan {
     int k_max = 0;
     int tile_rows = 0;
     int slots = 0;
+    int list_t = kListT;
 };
 
 struct Layout {
     size_t plan, q_a64, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list, fb_score,
-        fb_index, total;
+        fb_index, shared_thr, total;
 };
 
 bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
@@ -213,8 +214,9 @@ int scan_slots(const fs_db* db) {
     return tensor_scan(db) ? db->num_sms : db->num_sms * scan_fp32_ctas_per_sm();
 }
 
+// sizing != 0: plan the largest workspace any k could need (list size 16)
 fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const int32_t* k,
-                    Plan& pl) {
+                    Plan& pl, int sizing = 0) {
     const int n_seg = db->n_seg;
     if (q_seg_off) {
         if (q_seg_off[0] != 0 || q_seg_off[n_seg] != nq)
@@ -247,6 +249,8 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.lists = lists;
         work += (int64_t)p.qtiles * ceil_div(p.nrows, pl.tile_rows);
     }
+    // the tensor-core scan keeps 8-entry lists when every k fits (fewer inserts)
+    pl.list_t = (tensor_scan(db) && !sizing && pl.k_max <= kListTSmall) ? kListTSmall : kListT;
     const int64_t desired = (int64_t)pl.slots * 4;
     const int64_t tiles_per_item = std::max<int64_t>(1, ceil_div(work, desired));
     int64_t item = 0, cand = 0;
@@ -258,9 +262,10 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.chunks = p.nrows > 0 ? (int32_t)ceil_div(p.nrows, p.chunk_rows) : 0;
         p.item0 = item;
         p.cand0 = cand;
+        p.list_t = pl.list_t;
         if (p.nq > 0 && p.nrows > 0) {
             item += (int64_t)p.qtiles * p.chunks;
-            cand += (int64_t)p.nq * p.chunks * p.lists * kListT;
+            cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
         }
         const Bounds b = score_bounds(db, db->r_max[s]);
         p.bound_scan = (float)b.scan;
@@ -292,6 +297,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.fb_list = take(sizeof(int32_t) * nq);
     L.fb_score = take(sizeof(double) * (size_t)nq * kFbChunks * FS_MAX_K);
     L.fb_index = take(sizeof(int32_t) * (size_t)nq * kFbChunks * FS_MAX_K);
+    L.shared_thr = take(sizeof(uint32_t) * nq);
     L.total = off;
     return L;
 }
@@ -365,6 +371,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.fb_list = (int32_t*)(ws + L.fb_list);
     c.fb_score = (double*)(ws + L.fb_score);
     c.fb_index = (int32_t*)(ws + L.fb_index);
+    c.shared_thr = (uint32_t*)(ws + L.shared_thr);
     c.exclude = exclude;
     c.out_idx = idx;
     c.out_dist = dist;
@@ -380,6 +387,8 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
                                   c.work_counter, cs));
         FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_a64, c.q_lowp, db->fl,
                                     c.q_scale, c.q_resid, db->prec, db->status, cs));
+        // 0 sorts below every order-mapped score
+        FS_CUDA(cudaMemsetAsync(c.shared_thr, 0, sizeof(uint32_t) * nq, cs));
         t.finish((int)ceil_div(db->n_seg, 256) + 1);
     }
     if (pl.total_items > 0) {
@@ -390,7 +399,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
             const int eb = db->prec == FS_BF16 ? 2 : 1;
             FS_CUDA(make_code_map(&map_q, c.q_lowp, round_up(nq, kTcQueryRows), db->fl, eb,
                                   kTcQueryRows));
-            FS_CUDA(launch_scan_tc(v, c, map_q, db->map_x, grid, cs));
+            FS_CUDA(launch_scan_tc(v, c, map_q, db->map_x, grid, pl.list_t, cs));
         } else {
             FS_CUDA(launch_scan_fp32(v, c, grid, cs));
         }
@@ -583,7 +592,7 @@ fs_status fs_workspace_size(const fs_db* db, int32_t nq, const int32_t* q_seg_of
     if (nq < 0) return fail(FS_EINVAL, "nq=%d is negative", nq);
     std::vector<int32_t> kk(db->n_seg, 1);
     Plan pl;
-    fs_status st = make_plan(db, nq, q_seg_off, kk.data(), pl);
+    fs_status st = make_plan(db, nq, q_seg_off, kk.data(), pl, 1);
     if (st != FS_OK) return st;
     *bytes = make_layout(db, nq, pl).total;
     return FS_OK;

@@ -17,7 +17,8 @@
 namespace fsk {
 
 constexpr int kWarp = 32;
-constexpr int kListT = 16;        // entries per candidate list (>= FS_MAX_K)
+constexpr int kListT = 16;        // largest candidate list (>= FS_MAX_K)
+constexpr int kListTSmall = 8;    // list size when every k <= 8
 constexpr int kWindow = 64;       // candidates the rerank takes per query
 constexpr int kQTile = 128;       // queries per scan work item
 constexpr int kFbChunks = 32;     // row chunks per query in the exact fallback
@@ -73,11 +74,13 @@ struct SegPlan {
     int32_t chunks;      // row chunks the scan splits the segment into
     int32_t chunk_rows;  // rows per chunk (a multiple of the scan tile)
     int32_t lists;       // candidate lists per (query, chunk)
+    int32_t list_t;      // entries per candidate list (8 or 16)
     float bound_scan;    // |approximate score - exact cosine| <= bound_scan
     float bound_rq;      //   + bound_rq * (query residual norm), per query
     float bound_rerank;  // same bound for the FP32 rescoring of the window
+    int32_t pad_;
 };
-static_assert(sizeof(SegPlan) == 72, "SegPlan layout");
+static_assert(sizeof(SegPlan) == 80, "SegPlan layout");
 
 // Read-only device view of a database and of one call's workspace.
 struct DbView {
@@ -110,6 +113,8 @@ struct CallView {
     double* fb_score;         // [nq][kFbChunks][FS_MAX_K]
     int32_t* fb_index;        // [nq][kFbChunks][FS_MAX_K]
     int32_t* work_counter;    // dynamic scan scheduler
+    uint32_t* shared_thr;     // [nq] per query: highest lowest-kept score of any
+                              // full candidate list so far (order-mapped bits)
     const int32_t* exclude;   // [nq] or NULL
     int32_t* out_idx;         // [nq][k_max]
     float* out_dist;          // [nq][k_max]
@@ -159,6 +164,6 @@ size_t scan_tc_smem_bytes();
 cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols,
                           int elem_bytes, int box_rows);
 cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
-                           const CUtensorMap& map_x, int grid, cudaStream_t st);
+                           const CUtensorMap& map_x, int grid, int list_t, cudaStream_t st);
 
 }  // namespace fsk

@@ -180,6 +180,7 @@ k_scan_fp32(DbView db, CallView call) {
             const int64_t qlocal = (int64_t)qtile * BQ + lq;
             uint64_t* dst = call.cand + p.cand0 +
                             ((qlocal * p.chunks + chunk) * p.lists + hf) * (int64_t)T;
+            // (this kernel always keeps lists of kListT = T entries)
 #pragma unroll
             for (int e = 0; e < T; ++e) dst[e] = sm.lists[e][tid];
         }

@@ -96,34 +96,62 @@ struct ListState {
     int min_slot;      // slot of thr_key
 };
 
-// Offers (score, row) to the list of epilogue thread et. Out of line: it
-// runs rarely, and one copy keeps the filter loop small.
+// Offers (score, row) to the LT-entry list of epilogue thread et. Out of
+// line: one copy, called with every lane that has a candidate at once.
+template <int LT>
 __device__ __noinline__ ListState list_offer(ListState st, uint64_t* lists, int et, float v,
                                              int64_t row, int64_t row_end, int64_t row0,
                                              int excl) {
     const int32_t li = (int32_t)(row - row0);
     if (row >= row_end || li == excl) return st;
     const uint64_t key = make_key(v, (uint32_t)li);
-    if (st.cnt < T) {
+    if (st.cnt < LT) {
         lists[st.cnt * 128 + et] = key;
         ++st.cnt;
-        if (st.cnt < T) return st;
+        if (st.cnt < LT) return st;
     } else if (key > st.thr_key) {
         lists[st.min_slot * 128 + et] = key;
     } else {
         return st;
     }
-    uint64_t mn = ~0ull;
-    for (int e = 0; e < T; ++e) {
-        const uint64_t x = lists[e * 128 + et];
-        if (x < mn) {
-            mn = x;
-            st.min_slot = e;
+    // new minimum: a tree over the slots (short dependency chain)
+    uint64_t k[LT];
+    int slot[LT];
+#pragma unroll
+    for (int e = 0; e < LT; ++e) {
+        k[e] = lists[e * 128 + et];
+        slot[e] = e;
+    }
+#pragma unroll
+    for (int w = LT / 2; w > 0; w >>= 1) {
+#pragma unroll
+        for (int e = 0; e < w; ++e) {
+            const bool lo = k[e + w] < k[e];
+            k[e] = lo ? k[e + w] : k[e];
+            slot[e] = lo ? slot[e + w] : slot[e];
         }
     }
-    st.thr_key = mn;
-    st.thr_s = key_score(mn);
+    st.thr_key = k[0];
+    st.min_slot = slot[0];
+    st.thr_s = key_score(k[0]);
     return st;
+}
+
+// v[j] for a run-time j in 0..63 by a 6-level select tree (the array stays in
+// registers; a dynamic index would move it to local memory).
+__device__ __forceinline__ float select64(const float (&v)[64], int j) {
+    float a[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) a[i] = (j & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (j & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (j & 4) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (j & 8) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) a[i] = (j & 16) ? a[2 * i + 1] : a[2 * i];
+    return (j & 32) ? a[1] : a[0];
 }
 
 // A bounded wait that ignores the abort flag (used to drain on the way out).
@@ -133,7 +161,7 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
         if (globaltimer() - t0 > kWaitLimitNs) break;
 }
 
-template <bool FP8>
+template <bool FP8, int LT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
           const __grid_constant__ CUtensorMap map_x, int kblocks) {
@@ -272,11 +300,16 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             st.cnt = 0;
             st.min_slot = 0;
 #pragma unroll
-            for (int e = 0; e < T; ++e) lists[e * 128 + et] = 0;
+            for (int e = 0; e < LT; ++e) lists[e * 128 + et] = 0;
 
+            float published = -INFINITY;
             for (int t = 0; t < w.ntiles; ++t, ++tcount) {
                 const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
                 const int64_t tile_row0 = w.row_begin + (int64_t)t * BN;
+                // the best lowest-kept score any full list of this query reached
+                // (any block); rows below it cannot reach the top k
+                const float shared_s =
+                    qvalid ? unord_f32(__ldcg(call.shared_thr + w.qbase + lq)) : INFINITY;
                 if (FP8) {
                     // stage the tile's row scales (rows past the data read as 0); every
                     // epilogue thread finished tile t-2, the last user of sx[acc], before
@@ -322,16 +355,32 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     }
                     const float m = fmaxf(fmaxf(fmaxf(gm[0], gm[1]), fmaxf(gm[2], gm[3])),
                                           fmaxf(fmaxf(gm[4], gm[5]), fmaxf(gm[6], gm[7])));
-                    if (__any_sync(0xffffffffu, qvalid && m >= st.thr_s)) {
+                    float thr = fmaxf(st.thr_s, shared_s);
+                    if (__any_sync(0xffffffffu, m >= thr)) {
+                        // this lane's passing columns, only in groups some lane passes
+                        uint64_t mask = 0;
 #pragma unroll
                         for (int g = 0; g < 8; ++g) {
-                            if (__any_sync(0xffffffffu, qvalid && gm[g] >= st.thr_s)) {
+                            if (__any_sync(0xffffffffu, gm[g] >= thr)) {
+                                uint32_t bits = 0;
 #pragma unroll
                                 for (int i = 0; i < 8; ++i) {
                                     const float sc = FP8 ? v[8 * g + i] * sq : v[8 * g + i];
-                                    if (qvalid && sc >= st.thr_s)
-                                        st = list_offer(st, lists, et, sc, tile_row0 + c0 + 8 * g + i,
+                                    bits |= (sc >= thr ? 1u : 0u) << i;
+                                }
+                                mask |= (uint64_t)bits << (8 * g);
+                            }
+                        }
+                        // every lane takes its next candidate in the same iteration
+                        while (__any_sync(0xffffffffu, mask != 0)) {
+                            if (mask != 0) {
+                                const int j = __ffsll((long long)mask) - 1;
+                                mask &= mask - 1;
+                                const float sc = FP8 ? select64(v, j) * sq : select64(v, j);
+                                if (sc >= thr) {
+                                    st = list_offer<LT>(st, lists, et, sc, tile_row0 + c0 + j,
                                                         w.row_end, w.p.row0, excl);
+                                    thr = fmaxf(st.thr_s, shared_s);
                                 }
                             }
                         }
@@ -340,12 +389,16 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bars.tmem_empty[acc]));
+                if (qvalid && st.cnt == LT && st.thr_s > published) {
+                    atomicMax(call.shared_thr + w.qbase + lq, ord_f32(st.thr_s));
+                    published = st.thr_s;
+                }
             }
             if (ok && qvalid) {
                 const int64_t qlocal = (int64_t)w.qtile * BM + lq;
-                uint64_t* dst = call.cand + w.p.cand0 + (qlocal * w.p.chunks + w.chunk) * (int64_t)T;
+                uint64_t* dst = call.cand + w.p.cand0 + (qlocal * w.p.chunks + w.chunk) * (int64_t)LT;
 #pragma unroll
-                for (int e = 0; e < T; ++e) dst[e] = lists[e * 128 + et];
+                for (int e = 0; e < LT; ++e) dst[e] = lists[e * 128 + et];
             }
         }
     }
@@ -395,28 +448,34 @@ cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int c
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+template <bool FP8, int LT>
+cudaError_t launch_variant(const DbView& db, const CallView& call, const CUtensorMap& map_q,
+                           const CUtensorMap& map_x, int grid, int kblocks, cudaStream_t st) {
+    static bool attr_set = false;
+    const size_t smem = scan_tc_smem_bytes();
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_scan_tc<FP8, LT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_scan_tc<FP8, LT><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
-                           const CUtensorMap& map_x, int grid, cudaStream_t st) {
+                           const CUtensorMap& map_x, int grid, int list_t, cudaStream_t st) {
     if (call.total_items == 0) return cudaSuccess;
     const bool fp8 = db.prec == FS_FP8_E4M3;
     const int kblocks = (int)(db.fl * (fp8 ? 1 : 2) / 128);
     if (kblocks < 1 || kblocks > kMaxKBlocks) return cudaErrorInvalidValue;
-    const size_t smem = scan_tc_smem_bytes();
-    static bool attr_set[2] = {false, false};
-    if (fp8) {
-        if (!attr_set[1]) {
-            cudaFuncSetAttribute(k_scan_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set[1] = true;
-        }
-        k_scan_tc<true><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
-    } else {
-        if (!attr_set[0]) {
-            cudaFuncSetAttribute(k_scan_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set[0] = true;
-        }
-        k_scan_tc<false><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
-    }
-    return cudaGetLastError();
+    if (list_t == kListTSmall)
+        return fp8 ? launch_variant<true, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st);
+    if (list_t == kListT)
+        return fp8 ? launch_variant<true, kListT>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListT>(db, call, map_q, map_x, grid, kblocks, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fsk

@@ -151,7 +151,8 @@ k_select(DbView db, CallView call) {
             }
         } else {
             const int nl = p.chunks * p.lists;
-            const int64_t ne = (int64_t)nl * kListT;
+            const int lt = p.list_t;
+            const int64_t ne = (int64_t)nl * lt;
             const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * ne;
 
             // 1. k-th best approximate key
@@ -174,8 +175,8 @@ k_select(DbView db, CallView call) {
             uint64_t tau = 0;
             for (int l = lane; l < nl; l += 32) {
                 uint64_t mn = ~0ull;
-                for (int e = 0; e < kListT; ++e) {
-                    uint64_t v = cand[(int64_t)l * kListT + e];
+                for (int e = 0; e < lt; ++e) {
+                    uint64_t v = cand[(int64_t)l * lt + e];
                     mn = v < mn ? v : mn;
                 }
                 if (mn != 0) tau = mn > tau ? mn : tau;   // full list
