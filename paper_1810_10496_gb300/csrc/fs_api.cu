@@ -204,8 +204,8 @@ struct Plan {
 };
 
 struct Layout {
-    size_t plan, q_a64, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list, fb_score,
-        fb_index, shared_thr, total;
+    size_t plan, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
+        fb_score, fb_index, shared_thr, total;
 };
 
 bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
@@ -288,6 +288,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     const size_t lw = db->prec == FS_BF16 ? 2 : 1;
     L.plan = take(sizeof(SegPlan) * pl.seg.size());
     L.q_a64 = take(sizeof(double) * nq);
+    L.q_ss = take(sizeof(float) * nq);
     L.q_unit = take(sizeof(float) * (size_t)nq * db->fu);
     L.q_lowp = take(lw * (size_t)round_up(nq, kTcQueryRows) * db->fl);
     L.q_scale = take(sizeof(float) * nq);
@@ -361,6 +362,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.plan = (const SegPlan*)(ws + L.plan);
     c.q_raw = q;
     c.q_a64 = (double*)(ws + L.q_a64);
+    c.q_ss = (float*)(ws + L.q_ss);
     c.q_unit = (float*)(ws + L.q_unit);
     c.q_lowp = ws + L.q_lowp;
     c.q_scale = (float*)(ws + L.q_scale);
@@ -385,7 +387,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
         StageTimer t(FS_STAGE_PREPARE, cs);
         FS_CUDA(launch_write_plan(pl.seg.data(), db->n_seg, (SegPlan*)(ws + L.plan), c.fb_count,
                                   c.work_counter, cs));
-        FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_a64, c.q_lowp, db->fl,
+        FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_ss, c.q_lowp, db->fl,
                                     c.q_scale, c.q_resid, db->prec, db->status, cs));
         // 0 sorts below every order-mapped score
         FS_CUDA(cudaMemsetAsync(c.shared_thr, 0, sizeof(uint32_t) * nq, cs));
@@ -558,8 +560,9 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
         FS_TRY_CUDA(cudaMemcpyAsync(db->raw, x, sizeof(float) * n * f, cudaMemcpyDeviceToDevice, cs));
         FS_TRY_CUDA(cudaMemsetAsync(db->resid, 0, sizeof(float) * n, cs));
     }
-    FS_TRY_CUDA(launch_prepare_rows(db->raw, n, f, db->unit, db->fu, db->b64, db->lowp, db->fl,
+    FS_TRY_CUDA(launch_prepare_rows(db->raw, n, f, db->unit, db->fu, nullptr, db->lowp, db->fl,
                                     db->scale, db->resid, prec, db->status, cs));
+    FS_TRY_CUDA(launch_norm64_rows(db->raw, n, f, db->b64, cs));
 
     // per-segment largest residual (bounds of the low-precision scans)
     FS_TRY(alloc((void**)&db->seg_off_dev, sizeof(int64_t) * (n_seg + 1), "segments"));

@@ -102,7 +102,8 @@ struct DbView {
 struct CallView {
     const SegPlan* plan;      // [n_seg], in query order
     const float* q_raw;       // [nq][f] caller's queries
-    double* q_a64;            // [nq] binary64 sum of squares of each query
+    double* q_a64;            // [nq] binary64 sum of squares (queries sent to the fallback)
+    float* q_ss;              // [nq] FP32 sum of squares (0 exactly for a zero query)
     float* q_unit;            // [nq][fu]
     void* q_lowp;             // [nq][fl]
     float* q_scale;           // [nq]
@@ -131,8 +132,9 @@ struct CallView {
 cudaError_t launch_normalize_public(const float* x, int64_t n, int f, int64_t ld,
                                     float* x_unit, float* inv_norm, cudaStream_t st);
 cudaError_t launch_prepare_rows(const float* x, int64_t n, int f, float* unit, int fu,
-                                double* b64, void* lowp, int fl, float* scale,
+                                float* ss_out, void* lowp, int fl, float* scale,
                                 float* resid, int prec, uint32_t* status, cudaStream_t st);
+cudaError_t launch_norm64_rows(const float* x, int64_t n, int f, double* b64, cudaStream_t st);
 cudaError_t launch_check_sequences(const int64_t* off, const int16_t* ids, int64_t n,
                                    int64_t total, uint32_t* status, cudaStream_t st);
 cudaError_t launch_segment_max(const float* v, const int64_t* seg_off_dev, int n_seg,

@@ -8,8 +8,7 @@
 // every element of the row is scaled by the same reciprocal norm.
 //
 // Per row the kernel also writes (when asked):
-//   - B = sum x_i^2 in binary64, summed sequentially for i = 0..F-1 without
-//     fused multiply-add (the exact-formula rescoring reuses it);
+//   - the FP32 sum of squares (exactly 0 only for an all-zero row);
 //   - the BF16 code of each unit element (round to nearest even), or the
 //     FP8 E4M3 code of u_i / s with s = max_i |u_i| / 448 (per-vector scale);
 //   - the residual norm r = ||u - dequantised(u)||_2, which bounds how far a
@@ -65,7 +64,7 @@ __global__ void k_normalize_public(const float* __restrict__ x, int64_t n, int f
 
 // prec: FS_FP32 (no codes), FS_BF16, FS_FP8_E4M3
 __global__ void k_prepare_rows(const float* __restrict__ x, int64_t n, int f,
-                               float* __restrict__ unit, int fu, double* __restrict__ b64,
+                               float* __restrict__ unit, int fu, float* __restrict__ ss_out,
                                void* __restrict__ lowp, int fl, float* __restrict__ scale,
                                float* __restrict__ resid, int prec, uint32_t* status) {
     int lane = threadIdx.x & 31;
@@ -94,16 +93,7 @@ __global__ void k_prepare_rows(const float* __restrict__ x, int64_t n, int f,
     float* ur = unit + row * (int64_t)fu;
     for (int i = lane; i < fu; i += 32) ur[i] = (ok && i < f) ? xr[i] * inv : 0.0f;
 
-    if (b64 && lane == 0) {
-        double b = 0.0;
-        if (ok) {
-            for (int i = 0; i < f; ++i) {
-                double v = (double)xr[i];
-                b = __dadd_rn(b, __dmul_rn(v, v));
-            }
-        }
-        b64[row] = b;
-    }
+    if (ss_out && lane == 0) ss_out[row] = ss;
 
     if (prec == FS_BF16) {
         __nv_bfloat16* lr = reinterpret_cast<__nv_bfloat16*>(lowp) + row * (int64_t)fl;
@@ -144,6 +134,37 @@ __global__ void k_prepare_rows(const float* __restrict__ x, int64_t n, int f,
     }
 }
 
+// B = sum x_i^2 in binary64, summed sequentially for i = 0..F-1 without fused
+// multiply-add (the exact formula of the result contract). One thread per
+// row, so every lane of the narrow binary64 pipe does useful work; the rows
+// are staged through shared memory 32 features at a time with coalesced
+// loads. Rows flagged invalid by k_prepare_rows are not special here: their
+// build fails as a whole.
+constexpr int kNormRows = 256;
+__global__ void __launch_bounds__(kNormRows)
+k_norm64_rows(const float* __restrict__ x, int64_t n, int f, double* __restrict__ b64) {
+    __shared__ float tile[kNormRows][33];
+    const int64_t row0 = (int64_t)blockIdx.x * kNormRows;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double b = 0.0;
+    for (int f0 = 0; f0 < f; f0 += 32) {
+        // warp w loads rows w, w+8, ... (32 consecutive features each)
+        for (int r = w; r < kNormRows; r += kNormRows / 32) {
+            const int64_t row = row0 + r;
+            tile[r][lane] = (row < n && f0 + lane < f) ? x[row * f + f0 + lane] : 0.0f;
+        }
+        __syncthreads();
+        const int m = min(32, f - f0);
+        for (int i = 0; i < m; ++i) {
+            const double v = (double)tile[threadIdx.x][i];
+            b = __dadd_rn(b, __dmul_rn(v, v));
+        }
+        __syncthreads();
+    }
+    const int64_t row = row0 + threadIdx.x;
+    if (row < n) b64[row] = b;
+}
+
 __global__ void k_check_sequences(const int64_t* __restrict__ off, const int16_t* __restrict__ ids,
                                   int64_t n, int64_t total, uint32_t* status) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,13 +201,19 @@ cudaError_t launch_normalize_public(const float* x, int64_t n, int f, int64_t ld
     return cudaGetLastError();
 }
 
-cudaError_t launch_prepare_rows(const float* x, int64_t n, int f, float* unit, int fu, double* b64,
-                                void* lowp, int fl, float* scale, float* resid, int prec,
-                                uint32_t* status, cudaStream_t st) {
+cudaError_t launch_prepare_rows(const float* x, int64_t n, int f, float* unit, int fu,
+                                float* ss_out, void* lowp, int fl, float* scale, float* resid,
+                                int prec, uint32_t* status, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int warps = 8;
     k_prepare_rows<<<(unsigned)ceil_div(n, warps), warps * 32, 0, st>>>(
-        x, n, f, unit, fu, b64, lowp, fl, scale, resid, prec, status);
+        x, n, f, unit, fu, ss_out, lowp, fl, scale, resid, prec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm64_rows(const float* x, int64_t n, int f, double* b64, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_norm64_rows<<<(unsigned)ceil_div(n, kNormRows), kNormRows, 0, st>>>(x, n, f, b64);
     return cudaGetLastError();
 }
 

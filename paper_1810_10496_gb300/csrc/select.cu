@@ -10,17 +10,22 @@
 //     approximate score t_k.
 //  2. Certify: every approximate score is within E of the true cosine. A
 //     list that filled up dropped rows scoring at most its lowest kept score
-//     tau; if tau + 2E < t_k for every full list, no dropped row can be among
-//     the k nearest. Otherwise the query goes to the exact fallback scan.
+//     tau (rows below a score another full list published were dropped too,
+//     and such a score never exceeds that list's final tau); if tau + 2E <
+//     t_k for every full list, no dropped row can be among the k nearest.
+//     Otherwise the query goes to the exact fallback scan.
 //  3. Window: only candidates with approximate score >= t_k - 2E can be in
 //     the top k (at most 64 are taken; more also sends the query to the
 //     fallback).
-//  4. For the BF16/FP8 scans, rescore the window in FP32 from the unit
-//     vectors (bound E_r) and keep those within 2 E_r of the k-th rescored
-//     value; for the FP32 scan the scan score already is that rescoring.
-//  5. Score the survivors with the binary64 formula (sequential sums, no
-//     fused multiply-add), rank them by (score desc, index asc), write k.
-//     Survivors beyond k are the near ties the binary64 step resolves.
+//  4. Rescore the window in FP32 from the unit vectors, with a warp-wide
+//     summation whose error bound E_r is small, and compute the distance as
+//     1/2 |u_q - u_x|^2, which has no cancellation near 0.
+//  5. Sort the window by rescored value. Neighbours closer than 2 E_r may be
+//     out of order; runs of such near ties that reach into the first k
+//     places are scored with the binary64 formula (sequential sums, no fused
+//     multiply-add) and reordered by (score desc, index asc). Everything
+//     else is already in its exact place, because its rescored gaps exceed
+//     the error of both neighbours.
 #include "fs_internal.cuh"
 
 namespace fsk {
@@ -107,12 +112,40 @@ __device__ __forceinline__ void write_padding(const CallView& call, int q, int f
 constexpr int kSelWarps = 8;
 
 struct SelShared {
-    int32_t widx[kSelWarps][kWindow];     // window rows (segment-local)
-    float wsc[kSelWarps][kWindow];        // window approximate / rescored scores
-    double w64[kSelWarps][kWindow];       // binary64 scores of the survivors
-    int32_t wsurv[kSelWarps][kWindow];    // survivor rows
+    int32_t widx[kSelWarps][kWindow];     // window rows (segment-local), scan order
+    float wsc[kSelWarps][kWindow];        // their FP32 rescored cosines
+    float wdist[kSelWarps][kWindow];      // their FP32 distances
+    int32_t sidx[kSelWarps][kWindow];     // window sorted by (rescored desc, row asc)
+    float ssc[kSelWarps][kWindow];
+    float sdist[kSelWarps][kWindow];
+    double s64[kSelWarps][kWindow];       // binary64 cosines of near-tie members
+    uint8_t tie[kSelWarps][kWindow];      // member of a near-tie cluster
+    int16_t cl_begin[kSelWarps][FS_MAX_K], cl_end[kSelWarps][FS_MAX_K];
     unsigned long long stats[kNumStats];
 };
+
+// binary64 A = sum q_i^2 and D = sum q_i x_i, sequential in i without fused
+// multiply-add, then s = D / sqrt(A B) (0 for a zero vector)
+__device__ double exact_cosine_ab(const float* __restrict__ q, const float* __restrict__ x, int f,
+                                  double b) {
+    double a = 0.0, d = 0.0;
+    for (int i = 0; i < f; ++i) {
+        const double qi = (double)q[i];
+        a = __dadd_rn(a, __dmul_rn(qi, qi));
+        d = __dadd_rn(d, __dmul_rn(qi, (double)x[i]));
+    }
+    if (a == 0.0 || b == 0.0) return 0.0;
+    return __ddiv_rn(d, __dsqrt_rn(__dmul_rn(a, b))) + 0.0;  // -0 becomes +0
+}
+
+__device__ double exact_norm2(const float* __restrict__ q, int f) {
+    double a = 0.0;
+    for (int i = 0; i < f; ++i) {
+        const double qi = (double)q[i];
+        a = __dadd_rn(a, __dmul_rn(qi, qi));
+    }
+    return a;
+}
 
 __global__ void __launch_bounds__(kSelWarps * 32)
 k_select(DbView db, CallView call) {
@@ -127,13 +160,12 @@ k_select(DbView db, CallView call) {
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
         const int excl = call.exclude ? call.exclude[q] : -1;
-        const double a64 = call.q_a64[q];
         const int nrows = (int)p.nrows;
         int nout = 0;
 
         if (nrows == 0) {
             nout = 0;
-        } else if (a64 == 0.0) {
+        } else if (call.q_ss[q] == 0.0f) {
             // zero query: every cosine is 0, so the lowest indices win (d = 1)
             int c = 0;
             for (int r = 0; r < nrows && c < k; ++r) {
@@ -196,10 +228,7 @@ k_select(DbView db, CallView call) {
                     bool in = v != 0 && (double)key_score(v) >= lo;
                     unsigned m = __ballot_sync(kFull, in);
                     int pos = nw + __popc(m & ((1u << lane) - 1));
-                    if (in && pos < kWindow) {
-                        sh.widx[wid][pos] = key_index(v);
-                        sh.wsc[wid][pos] = key_score(v);
-                    }
+                    if (in && pos < kWindow) sh.widx[wid][pos] = key_index(v);
                     nw += __popc(m);
                 }
                 if (nw > kWindow) certified = false;
@@ -210,82 +239,118 @@ k_select(DbView db, CallView call) {
                 if (lane == 0) {
                     int slot = atomicAdd(call.fb_count, 1);
                     call.fb_list[slot] = q;
+                    call.q_a64[q] = exact_norm2(call.q_raw + (int64_t)q * db.f, db.f);
                 }
                 nout = -1;  // the fallback writes this query
             } else {
-                // 4. FP32 rescoring of the window (BF16/FP8 scans)
-                double lo2 = -INFINITY;
-                if (db.prec != FS_FP32) {
-                    const float* qu = call.q_unit + (int64_t)q * db.fu;
-                    for (int w = 0; w < nw; ++w) {
-                        const float* xu = db.unit + (p.row0 + sh.widx[wid][w]) * (int64_t)db.fu;
-                        float acc = 0.0f;
-                        for (int i = lane; i < db.fu; i += 32) acc = fmaf(qu[i], xu[i], acc);
+                // 4. FP32 rescoring of the window: the cosine of the unit vectors and
+                //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
+                const float* qu = call.q_unit + (int64_t)q * db.fu;
+                for (int w = 0; w < nw; ++w) {
+                    const int64_t row = p.row0 + sh.widx[wid][w];
+                    const float* xu = db.unit + row * (int64_t)db.fu;
+                    float dot = 0.0f, dd = 0.0f;
+                    for (int i = lane; i < db.fu; i += 32) {
+                        const float a = qu[i], b = xu[i];
+                        dot = fmaf(a, b, dot);
+                        const float t = a - b;
+                        dd = fmaf(t, t, dd);
+                    }
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-                        acc = __shfl_sync(kFull, acc, 0);
-                        if (lane == 0) sh.wsc[wid][w] = acc;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        dot += __shfl_xor_sync(kFull, dot, o);
+                        dd += __shfl_xor_sync(kFull, dd, o);
+                    }
+                    if (lane == 0) {
+                        sh.wsc[wid][w] = dot;
+                        // a zero row has cosine 0 by convention: d = 1
+                        sh.wdist[wid][w] = db.b64[row] == 0.0 ? 1.0f : 0.5f * dd;
+                    }
+                }
+                __syncwarp();
+                // 5. sort the window by (rescored desc, row asc)
+                for (int w = lane; w < nw; w += 32) {
+                    const float sw = sh.wsc[wid][w];
+                    const int rw = sh.widx[wid][w];
+                    int rank = 0;
+                    for (int v = 0; v < nw; ++v) {
+                        const float sv = sh.wsc[wid][v];
+                        rank += (sv > sw) || (sv == sw && sh.widx[wid][v] < rw);
+                    }
+                    sh.sidx[wid][rank] = rw;
+                    sh.ssc[wid][rank] = sw;
+                    sh.sdist[wid][rank] = sh.wdist[wid][w];
+                    sh.tie[wid][rank] = 0;
+                }
+                __syncwarp();
+                // 6. near-tie clusters reaching into the first k places: runs whose
+                //    neighbouring rescored values differ by at most 2 E_r
+                int ncl = 0, nfp = 0;
+                if (lane == 0) {
+                    const double er2 = 2.0 * (double)p.bound_rerank;
+                    int pos = 0;
+                    const int lim = min(k, nw);
+                    while (pos < lim) {
+                        int end = pos + 1;
+                        while (end < nw && (double)sh.ssc[wid][end - 1] - (double)sh.ssc[wid][end] <= er2)
+                            ++end;
+                        if (end - pos >= 2) {
+                            sh.cl_begin[wid][ncl] = (int16_t)pos;
+                            sh.cl_end[wid][ncl] = (int16_t)end;
+                            ++ncl;
+                            for (int m = pos; m < end; ++m) sh.tie[wid][m] = 1;
+                            nfp += end - pos;
+                        }
+                        pos = end;
+                    }
+                }
+                ncl = __shfl_sync(kFull, ncl, 0);
+                nfp = __shfl_sync(kFull, nfp, 0);
+                __syncwarp();
+                // 7. binary64 scores of the cluster members, one lane each
+                if (ncl > 0) {
+                    const float* qr = call.q_raw + (int64_t)q * db.f;
+                    for (int m = lane; m < nw; m += 32) {
+                        if (sh.tie[wid][m]) {
+                            const int64_t row = p.row0 + sh.sidx[wid][m];
+                            sh.s64[wid][m] = exact_cosine_ab(qr, db.raw + row * db.f, db.f, db.b64[row]);
+                        }
                     }
                     __syncwarp();
-                    if (lane == 0) atomicAdd(&sh.stats[kStatRerank], (unsigned long long)nw);
-                    // k-th largest rescored value
-                    // k-th largest rescored value, counting repeated values
-                    float prevv = INFINITY, kv = -INFINITY;
-                    int taken = 0;
-                    while (taken < k && taken < nw) {
-                        float m = -INFINITY;
-                        for (int w = lane; w < nw; w += 32) {
-                            float v = sh.wsc[wid][w];
-                            if (v < prevv && v > m) m = v;
+                    // order each cluster by (binary64 desc, row asc)
+                    if (lane == 0) {
+                        for (int c = 0; c < ncl; ++c) {
+                            const int b = sh.cl_begin[wid][c], e = sh.cl_end[wid][c];
+                            for (int i = b + 1; i < e; ++i) {
+                                const double si = sh.s64[wid][i];
+                                const int ri = sh.sidx[wid][i];
+                                int j = i;
+                                while (j > b && better(si, ri, sh.s64[wid][j - 1], sh.sidx[wid][j - 1])) {
+                                    sh.s64[wid][j] = sh.s64[wid][j - 1];
+                                    sh.sidx[wid][j] = sh.sidx[wid][j - 1];
+                                    --j;
+                                }
+                                sh.s64[wid][j] = si;
+                                sh.sidx[wid][j] = ri;
+                            }
                         }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-                        int c = 0;
-                        for (int w = lane; w < nw; w += 32) c += sh.wsc[wid][w] == m;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-                        prevv = m;
-                        kv = m;
-                        taken += c;
                     }
-                    lo2 = (double)kv - 2.0 * (double)p.bound_rerank;
+                    __syncwarp();
                 }
-
-                // 5. binary64 scores of the survivors
-                int ns = 0;
-                for (int w0 = 0; w0 < nw; w0 += 32) {
-                    const int w = w0 + lane;
-                    bool in = w < nw && (double)sh.wsc[wid][w] >= lo2;
-                    unsigned m = __ballot_sync(kFull, in);
-                    int pos = ns + __popc(m & ((1u << lane) - 1));
-                    if (in) sh.wsurv[wid][pos] = sh.widx[wid][w];
-                    ns += __popc(m);
+                // 8. the first k places
+                nout = min(nw, k);
+                for (int c = lane; c < nout; c += 32) {
+                    call.out_idx[out0 + c] = sh.sidx[wid][c];
+                    float d = sh.sdist[wid][c];
+                    if (sh.tie[wid][c]) d = (float)(1.0 - sh.s64[wid][c]);
+                    call.out_dist[out0 + c] = d;
                 }
-                __syncwarp();
-                const float* qr = call.q_raw + (int64_t)q * db.f;
-                for (int w = lane; w < ns; w += 32) {
-                    const int64_t row = p.row0 + sh.wsurv[wid][w];
-                    sh.w64[wid][w] = exact_cosine(qr, db.raw + row * db.f, db.f, a64, db.b64[row]);
-                }
-                __syncwarp();
-                // rank by (score desc, index asc)
-                for (int w = lane; w < ns; w += 32) {
-                    const double s = sh.w64[wid][w];
-                    const int r = sh.wsurv[wid][w];
-                    int rank = 0;
-                    for (int v = 0; v < ns; ++v)
-                        rank += better(sh.w64[wid][v], sh.wsurv[wid][v], s, r);
-                    if (rank < k) {
-                        call.out_idx[out0 + rank] = r;
-                        call.out_dist[out0 + rank] = (float)(1.0 - s);
-                    }
-                }
-                nout = min(ns, k);
                 if (lane == 0) {
                     atomicAdd(&sh.stats[kStatQueries], 1ull);
                     atomicAdd(&sh.stats[kStatCertified], 1ull);
-                    atomicAdd(&sh.stats[kStatFp64], (unsigned long long)ns);
-                    atomicAdd(&sh.stats[kStatNearTies], (unsigned long long)(ns - nout));
+                    atomicAdd(&sh.stats[kStatRerank], (unsigned long long)nw);
+                    atomicAdd(&sh.stats[kStatFp64], (unsigned long long)nfp);
+                    atomicAdd(&sh.stats[kStatNearTies], (unsigned long long)ncl);
                 }
             }
         }
