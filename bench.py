@@ -41,9 +41,12 @@ UNIT = "pairs/s"
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
-# capture of the current kernel, keyed by (kernel, workload, precision);
-# None until captured. Source: profiles/*.md
-TRAFFIC_BYTES = {}
+# capture of the current version of that kernel, keyed by (kernel, workload,
+# precision); absent (reported as null) until captured. Source: the matching
+# summary under profiles/.
+TRAFFIC_BYTES = {
+    ("scan_fp32", "fp32_scale", "fp32"): 650.46e6,   # profiles/scan_fp32_fp32_scale.md
+}
 
 
 def log(*a):
@@ -374,7 +377,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fp32_scale", choices=sorted(fsgen.CONFIGS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")

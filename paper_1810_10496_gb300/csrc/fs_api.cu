@@ -228,7 +228,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         return fail(FS_EINVAL, "the database has %d segments: q_seg_off is required", n_seg);
     }
     pl.tile_rows = tensor_scan(db) ? kTcTileRows : kFp32TileRows;
-    const int lists = tensor_scan(db) ? 1 : kFp32Lists;
+    const int lists = tensor_scan(db) ? kTcLists : kFp32Lists;
     pl.slots = std::max(1, scan_slots(db));
     pl.seg.resize(n_seg);
     pl.k_max = 0;

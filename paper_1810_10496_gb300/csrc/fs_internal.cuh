@@ -162,6 +162,7 @@ int scan_fp32_ctas_per_sm();
 // scan_tc.cu (tcgen05 scan of BF16 / FP8 codes)
 constexpr int kTcTileRows = 256;
 constexpr int kTcQueryRows = 128;
+constexpr int kTcLists = 2;        // candidate lists per (query, chunk): tile halves
 size_t scan_tc_smem_bytes();
 cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols,
                           int elem_bytes, int box_rows);

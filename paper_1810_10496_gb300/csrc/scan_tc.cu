@@ -13,10 +13,13 @@
 //     in tensor memory, double buffered (2 x 256 of the 512 columns) so the
 //     epilogue of one tile overlaps the MMAs of the next.
 //   * Warp 0 issues the TMA loads, warp 1 (one thread) issues tcgen05.mma,
-//     warps 2-5 are the epilogue: thread i owns query i of the tile (TMEM
-//     lane i), reads its 256 scores with tcgen05.ld and keeps its 16 best
-//     (score, row) pairs in shared memory, tested against a running
-//     threshold with one max per 64 scores in the common case.
+//     warps 2-9 are the epilogue, two per TMEM lane quarter: a thread owns
+//     one query of the tile (its TMEM lane) and one half of each tile's 256
+//     columns, reads its 128 scores with tcgen05.ld and keeps its 8 or 16
+//     best (score, row) pairs in registers, tested against a running
+//     threshold with one max per 64 scores in the common case. A block
+//     also drops rows below the best threshold any block has published for
+//     the query; lanes with candidates insert them together.
 //   * FP8 scores are acc * s_row * s_query (per-vector scales, Sec. 4.2's
 //     cosine of the dequantised vectors); BF16 scores are acc itself.
 //
@@ -38,14 +41,15 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                // two per TMEM lane quarter
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = 64 + kEpiThreads;  // + TMA warp + MMA warp
 constexpr int BM = 128;                     // queries per tile (MMA M)
 constexpr int BN = kTcTileRows;             // database rows per tile (MMA N)
 constexpr int kStages = 4;
 constexpr uint32_t kStageBytes = BN * 128;  // one 128-byte K block of BN rows
 constexpr uint32_t kABlockBytes = BM * 128; // one 128-byte K block of BM queries
 constexpr int kMaxKBlocks = 4;              // 256 BF16 or 512 FP8 features
-constexpr int T = kListT;
 constexpr uint32_t kTmemCols = 2 * BN;
 
 struct Bars {
@@ -88,54 +92,68 @@ __device__ __forceinline__ Item decode(const CallView& call, int64_t item) {
     return it;
 }
 
-// Running state of one thread's candidate list (16 keys in shared memory).
-struct ListState {
+// One thread's candidate list, held in registers: LT keys (every index is a
+// compile-time constant, so the array never leaves the register file).
+template <int LT>
+struct RegList {
+    uint64_t k[LT];
     uint64_t thr_key;  // lowest key kept once the list is full (0 before)
     float thr_s;       // its score; -inf while the list is filling
     int cnt;           // keys stored so far
     int min_slot;      // slot of thr_key
-};
 
-// Offers (score, row) to the LT-entry list of epilogue thread et. Out of
-// line: one copy, called with every lane that has a candidate at once.
-template <int LT>
-__device__ __noinline__ ListState list_offer(ListState st, uint64_t* lists, int et, float v,
-                                             int64_t row, int64_t row_end, int64_t row0,
-                                             int excl) {
-    const int32_t li = (int32_t)(row - row0);
-    if (row >= row_end || li == excl) return st;
-    const uint64_t key = make_key(v, (uint32_t)li);
-    if (st.cnt < LT) {
-        lists[st.cnt * 128 + et] = key;
-        ++st.cnt;
-        if (st.cnt < LT) return st;
-    } else if (key > st.thr_key) {
-        lists[st.min_slot * 128 + et] = key;
-    } else {
-        return st;
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int e = 0; e < LT; ++e) k[e] = 0;
+        thr_key = 0;
+        thr_s = -INFINITY;
+        cnt = 0;
+        min_slot = 0;
     }
-    // new minimum: a tree over the slots (short dependency chain)
-    uint64_t k[LT];
-    int slot[LT];
+
+    // new minimum: a tree over the slots
+    __device__ __forceinline__ void recompute() {
+        uint64_t m[LT];
+        int slot[LT];
 #pragma unroll
-    for (int e = 0; e < LT; ++e) {
-        k[e] = lists[e * 128 + et];
-        slot[e] = e;
-    }
-#pragma unroll
-    for (int w = LT / 2; w > 0; w >>= 1) {
-#pragma unroll
-        for (int e = 0; e < w; ++e) {
-            const bool lo = k[e + w] < k[e];
-            k[e] = lo ? k[e + w] : k[e];
-            slot[e] = lo ? slot[e + w] : slot[e];
+        for (int e = 0; e < LT; ++e) {
+            m[e] = k[e];
+            slot[e] = e;
         }
+#pragma unroll
+        for (int w = LT / 2; w > 0; w >>= 1) {
+#pragma unroll
+            for (int e = 0; e < w; ++e) {
+                const bool lo = m[e + w] < m[e];
+                m[e] = lo ? m[e + w] : m[e];
+                slot[e] = lo ? slot[e + w] : slot[e];
+            }
+        }
+        thr_key = m[0];
+        min_slot = slot[0];
+        thr_s = key_score(m[0]);
     }
-    st.thr_key = k[0];
-    st.min_slot = slot[0];
-    st.thr_s = key_score(k[0]);
-    return st;
-}
+
+    // Offers (score, row): kept if the list is filling or it beats the lowest.
+    __device__ __forceinline__ void offer(float v, int64_t row, int64_t row_end, int64_t row0,
+                                          int excl) {
+        const int32_t li = (int32_t)(row - row0);
+        if (row >= row_end || li == excl) return;
+        const uint64_t key = make_key(v, (uint32_t)li);
+        int at;
+        if (cnt < LT) {
+            at = cnt++;
+        } else if (key > thr_key) {
+            at = min_slot;
+        } else {
+            return;
+        }
+#pragma unroll
+        for (int e = 0; e < LT; ++e)
+            if (e == at) k[e] = key;
+        if (cnt == LT) recompute();
+    }
+};
 
 // v[j] for a run-time j in 0..63 by a 6-level select tree (the array stays in
 // registers; a dynamic index would move it to local memory).
@@ -175,8 +193,6 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t a_smem = base;
     const uint32_t b_smem = a_smem + kMaxKBlocks * kABlockBytes;
-    uint64_t* lists = reinterpret_cast<uint64_t*>(
-        smem_raw + (b_smem + kStages * kStageBytes - smem_u32(smem_raw)));
     constexpr int kElemsPerKBlock = FP8 ? 128 : 64;
     const uint32_t idesc = FP8 ? kIdescE4m3 : kIdescBf16;
 
@@ -188,13 +204,13 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&bars.tmem_full[a]), 1);
-            mbar_init(smem_u32(&bars.tmem_empty[a]), 4 * 32);
+            mbar_init(smem_u32(&bars.tmem_empty[a]), kEpiThreads);
         }
         mbar_init(smem_u32(&bars.a_full), 1);
         mbar_init(smem_u32(&bars.a_empty), 1);
         mbar_init(smem_u32(&bars.drain), 1);
-        mbar_init(smem_u32(&bars.sx_ready[0]), 4 * 32);
-        mbar_init(smem_u32(&bars.sx_ready[1]), 4 * 32);
+        mbar_init(smem_u32(&bars.sx_ready[0]), kEpiThreads);
+        mbar_init(smem_u32(&bars.sx_ready[1]), kEpiThreads);
         fence_barrier_init();
     }
     if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), kTmemCols);
@@ -286,7 +302,9 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;              // TMEM lanes this warp may read
         const int lq = quarter * 32 + lane;        // query row of the tile
-        const int et = threadIdx.x - 64;           // epilogue thread 0..127
+        const int et = threadIdx.x - 64;           // epilogue thread 0..255
+        const int half = (warp - 2) >> 2;          // which half of each tile's columns
+        constexpr int kHalfCols = BN / 2;
         uint32_t tcount = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; ok && item < call.total_items; item += gridDim.x) {
@@ -294,27 +312,25 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             const bool qvalid = lq < w.nq_tile;
             const int excl = (call.exclude && qvalid) ? call.exclude[w.qbase + lq] : -1;
             const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
-            ListState st;
-            st.thr_key = 0;
-            st.thr_s = -INFINITY;
-            st.cnt = 0;
-            st.min_slot = 0;
-#pragma unroll
-            for (int e = 0; e < LT; ++e) lists[e * 128 + et] = 0;
+            RegList<LT> st;
+            st.reset();
 
             float published = -INFINITY;
+            // the best lowest-kept score any full list of this query reached (any
+            // block); rows below it cannot reach the top k. It is read one tile
+            // ahead so the L2 round trip overlaps the current tile.
+            const uint32_t* shared_p = call.shared_thr + w.qbase + lq;
+            uint32_t shared_next = qvalid ? __ldcg(shared_p) : 0xffffffffu;
             for (int t = 0; t < w.ntiles; ++t, ++tcount) {
                 const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
                 const int64_t tile_row0 = w.row_begin + (int64_t)t * BN;
-                // the best lowest-kept score any full list of this query reached
-                // (any block); rows below it cannot reach the top k
-                const float shared_s =
-                    qvalid ? unord_f32(__ldcg(call.shared_thr + w.qbase + lq)) : INFINITY;
+                const float shared_s = qvalid ? unord_f32(shared_next) : INFINITY;
+                if (qvalid && t + 1 < w.ntiles) shared_next = __ldcg(shared_p);
                 if (FP8) {
                     // stage the tile's row scales (rows past the data read as 0); every
                     // epilogue thread finished tile t-2, the last user of sx[acc], before
                     // any thread could complete the phase of tile t-1
-                    for (int j = et; j < BN; j += 128) {
+                    for (int j = et; j < BN; j += kEpiThreads) {
                         const int64_t r = tile_row0 + j;
                         sx[acc][j] = r < w.row_end ? db.scale[r] : 0.0f;
                     }
@@ -329,7 +345,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 64) {
+                for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 64) {
                     uint32_t r0[32], r1[32];
                     tmem_ld_32x32b_x32(taddr + c0, r0);
                     tmem_ld_32x32b_x32(taddr + c0 + 32, r1);
@@ -378,8 +394,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                 mask &= mask - 1;
                                 const float sc = FP8 ? select64(v, j) * sq : select64(v, j);
                                 if (sc >= thr) {
-                                    st = list_offer<LT>(st, lists, et, sc, tile_row0 + c0 + j,
-                                                        w.row_end, w.p.row0, excl);
+                                    st.offer(sc, tile_row0 + c0 + j, w.row_end, w.p.row0, excl);
                                     thr = fmaxf(st.thr_s, shared_s);
                                 }
                             }
@@ -396,9 +411,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             }
             if (ok && qvalid) {
                 const int64_t qlocal = (int64_t)w.qtile * BM + lq;
-                uint64_t* dst = call.cand + w.p.cand0 + (qlocal * w.p.chunks + w.chunk) * (int64_t)LT;
+                uint64_t* dst = call.cand + w.p.cand0 +
+                                ((qlocal * w.p.chunks + w.chunk) * 2 + half) * (int64_t)LT;
 #pragma unroll
-                for (int e = 0; e < LT; ++e) dst[e] = lists[e * 128 + et];
+                for (int e = 0; e < LT; ++e) dst[e] = st.k[e];
             }
         }
     }
@@ -428,7 +444,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 size_t scan_tc_smem_bytes() {
-    return 1024 + kMaxKBlocks * kABlockBytes + kStages * kStageBytes + T * 128 * sizeof(uint64_t);
+    return 1024 + kMaxKBlocks * kABlockBytes + kStages * kStageBytes;
 }
 
 // 2-D tensor map of a row-major [rows][cols] array of 1- or 2-byte codes,
