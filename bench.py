@@ -132,44 +132,76 @@ def setup_dist():
 
 
 def workload_desc(w):
+    if w.n_seg > 1:
+        return (f"{w.name}: {w.n_seg} databases, {w.n:,} rows x {w.f} features in all, "
+                f"{w.q:,} queries, k in {sorted(set(w.k))} per database, phase orders 1-128 "
+                f"int16 pass IDs")
     return (f"{w.name}: database {w.n:,} x {w.f} features, {w.q:,} queries, "
-            f"k={w.k[0] if w.n_seg == 1 else 'per segment'}, phase orders 1-128 int16 pass IDs")
+            f"k={w.k[0]}, phase orders 1-128 int16 pass IDs")
+
+
+def segment_arrays(w):
+    """Per-query segment, its row range and k (one segment when unsegmented)."""
+    if w.n_seg == 1:
+        return (np.zeros(w.q, np.int64), np.array([0, w.n], np.int64),
+                np.array([0, w.q], np.int64), np.array(w.k[:1], np.int64))
+    seg_of_q = np.repeat(np.arange(w.n_seg), np.diff(w.q_seg_off))
+    return seg_of_q, w.seg_off.astype(np.int64), w.q_seg_off.astype(np.int64), np.array(w.k)
+
+
+def pair_count(w):
+    _, so, qo, _ = segment_arrays(w)
+    return int(np.sum(np.diff(so) * np.diff(qo)))
 
 
 def oracle_sample(w, nq_sample, seed=0):
-    """Time the CPU oracle on a sample of the queries against the whole
-    database (the oracle as it stands)."""
+    """Time the CPU oracle (as it stands) on a sample of the queries, each
+    against its whole database. Returns the picked queries, the oracle's
+    (idx, dist, seqs, lens) per picked query, the seconds and the pairs."""
     import oracle
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(w.q, size=min(nq_sample, w.q), replace=False))
+    seg_of_q, so, qo, ks = segment_arrays(w)
+    out = {}
+    pairs = 0
     t0 = time.perf_counter()
-    i_o, d_o, s_o, l_o = oracle.recommend(w.x, w.queries[pick], w.k[0], w.seq_off, w.seq_ids, 128)
+    for s in np.unique(seg_of_q[pick]):
+        qs = pick[seg_of_q[pick] == s]
+        lo, hi = int(so[s]), int(so[s + 1])
+        off = w.seq_off[lo:hi + 1] - w.seq_off[lo]
+        ids = w.seq_ids[w.seq_off[lo]:w.seq_off[hi]]
+        res = oracle.recommend(w.x[lo:hi], w.queries[qs], int(ks[s]), off, ids, 128)
+        for j, q in enumerate(qs):
+            out[int(q)] = tuple(r[j] for r in res)
+        pairs += len(qs) * (hi - lo)
     dt = time.perf_counter() - t0
-    return pick, (i_o, d_o, s_o, l_o), dt
+    return pick, out, dt, pairs
 
 
 def run_reference(args):
     world, rank, _ = setup_dist()
     if rank != 0:
         return 0
-    w = fsgen.make(args.workload, workers=min(16, _NCPU))
-    times = []
+    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
+    times, pairs = [], 0
     for s in range(args.warmup + args.steps):
-        _, _, dt = oracle_sample(w, args.ref_sample, seed=s)
+        _, _, dt, pr = oracle_sample(w, args.ref_sample, seed=s)
         if s >= args.warmup:
             times.append(dt)
+            pairs += pr
     nq = min(args.ref_sample, w.q)
-    sec = float(np.mean(times))
-    value = nq * w.n / sec
+    sec = float(np.sum(times))
+    value = pairs / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "sample": f"{nq} queries per step"},
-        "queries_per_s": nq / sec,
+        "queries_per_s": nq * args.steps / sec,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": _NCPU, "kind": "oracle",
-                         "sample": f"{nq} of {w.q:,} queries against all {w.n:,} rows per step"},
+                         "sample": f"{nq} of {w.q:,} queries per step, each against its whole "
+                                   f"database"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -195,11 +227,16 @@ def run_ours(args):
     fs.lib()
 
     t0 = time.perf_counter()
-    w = fsgen.make(args.workload, workers=min(16, _NCPU))
+    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
     log(f"[rank {rank}] workload generated in {time.perf_counter() - t0:.1f} s")
-    k = w.k[0]
+    ks = np.array(w.k, dtype=np.int32)
+    k_max = int(ks.max())
+    seg_off = w.seg_off if w.n_seg > 1 else None
+    q_seg_off = w.q_seg_off if w.n_seg > 1 else None
     Q, N, F = w.q, w.n, w.f
     l_max = 128
+    pairs = pair_count(w)
+    use_graph = args.graph if args.graph is not None else (w.n_seg > 1)
 
     x_d = torch.from_numpy(w.x).to(dev)
     off_d = torch.from_numpy(w.seq_off).to(dev)
@@ -208,25 +245,41 @@ def run_ours(args):
     q_d = q_host.to(dev)
 
     def make_db(prec):
-        db = fs.fs_build_db(x_d, off_d, ids_d, prec=prec)
-        ws = torch.empty(fs.fs_workspace_size(db, Q), dtype=torch.uint8, device=dev)
+        db = fs.fs_build_db(x_d, off_d, ids_d, seg_off=seg_off, prec=prec)
+        ws = torch.empty(fs.fs_workspace_size(db, Q, q_seg_off), dtype=torch.uint8, device=dev)
         return db, ws
 
-    outs = dict(idx=torch.empty((Q, k), dtype=torch.int32, device=dev),
-                dist=torch.empty((Q, k), dtype=torch.float32, device=dev),
-                seq_out=torch.empty((Q, k, l_max), dtype=torch.int16, device=dev),
-                seq_len=torch.empty((Q, k), dtype=torch.int32, device=dev))
+    outs = dict(idx=torch.empty((Q, k_max), dtype=torch.int32, device=dev),
+                dist=torch.empty((Q, k_max), dtype=torch.float32, device=dev),
+                seq_out=torch.empty((Q, k_max, l_max), dtype=torch.int16, device=dev),
+                seq_len=torch.empty((Q, k_max), dtype=torch.int32, device=dev))
 
     def step(db, ws, q):
-        fs.fs_recommend(db, q, k, workspace=ws, l_max=l_max, **outs)
+        fs.fs_recommend(db, q, ks, q_seg_off=q_seg_off, workspace=ws, l_max=l_max, **outs)
 
-    def timed(db, ws, steps, warmup, sample_clocks=False):
+    def timed(db, ws, steps, warmup, sample_clocks=False, graph=False):
+        """Time `steps` steps (events around each); per-stage times and launch
+        counts come from eager steps with the library's stage timing on."""
         stream = torch.cuda.current_stream()
         for _ in range(warmup):
             step(db, ws, q_d)
         torch.cuda.synchronize()
+        g = None
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step(db, ws, q_d)
+            g.replay()
+            torch.cuda.synchronize()
+        # eager, profiled steps: stage times and kernel launches per step
         fs.fs_profile_read(reset=True)
         fs.fs_profile_enable(True)
+        for _ in range(max(3, min(steps, 10))):
+            step(db, ws, q_d)
+        torch.cuda.synchronize()
+        fs.fs_profile_enable(False)
+        prof = fs.fs_profile_read(reset=True)
+        launches_per_step = prof["launches"] / max(1, prof["calls"]["prepare"])
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
         if world > 1:
@@ -240,7 +293,10 @@ def run_ours(args):
         g0.record(stream)
         for a, b in evs:
             a.record(stream)
-            step(db, ws, q_d)
+            if g is not None:
+                g.replay()
+            else:
+                step(db, ws, q_d)
             b.record(stream)
         g1.record(stream)
         torch.cuda.synchronize()
@@ -248,16 +304,17 @@ def run_ours(args):
             tdist.barrier()
         if sampler:
             sampler.__exit__(None, None, None)
-        fs.fs_profile_enable(False)
-        prof = fs.fs_profile_read(reset=True)
         per = [a.elapsed_time(b) for a, b in evs]
         total = g0.elapsed_time(g1)
-        return total, per, prof, (sampler.summary() if sampler else None)
+        return total, per, prof, launches_per_step, (sampler.summary() if sampler else None)
 
     prec = args.precision
+    t0 = time.perf_counter()
     db, ws = make_db(prec)
+    build_s = time.perf_counter() - t0
     fs.fs_db_stats(db, reset=True)
-    total_ms, per, prof, clocks = timed(db, ws, args.steps, args.warmup, sample_clocks=True)
+    total_ms, per, prof, lps, clocks = timed(db, ws, args.steps, args.warmup,
+                                             sample_clocks=True, graph=use_graph)
     st = fs.fs_db_stats(db)
     fs.fs_db_check(db)
     if world > 1:
@@ -265,12 +322,11 @@ def run_ours(args):
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
-    pairs = Q * N
     value = world * pairs * args.steps / (total_ms / 1e3)
 
     # dominant kernel: the scan (one launch per step)
     scan_ms = prof["ms"]["scan"] / max(1, prof["calls"]["scan"])
-    flops = 2.0 * Q * N * F
+    flops = 2.0 * pairs * F
     peaks, peak_src = load_peaks()
     if prec == "fp32":
         roof = {"bound": "alu", "achieved": flops / (scan_ms / 1e3) / 1e12,
@@ -288,15 +344,15 @@ def run_ours(args):
     roof["stage_ms_per_step"] = {s: prof["ms"][s] / max(1, prof["calls"][s]) for s in prof["ms"]}
 
     # end to end through the public API from host buffers
-    idx_h = torch.empty((Q, k), dtype=torch.int32).pin_memory()
-    dist_h = torch.empty((Q, k), dtype=torch.float32).pin_memory()
-    seq_h = torch.empty((Q, k, l_max), dtype=torch.int16).pin_memory()
-    len_h = torch.empty((Q, k), dtype=torch.int32).pin_memory()
+    idx_h = torch.empty((Q, k_max), dtype=torch.int32).pin_memory()
+    dist_h = torch.empty((Q, k_max), dtype=torch.float32).pin_memory()
+    seq_h = torch.empty((Q, k_max, l_max), dtype=torch.int16).pin_memory()
+    len_h = torch.empty((Q, k_max), dtype=torch.int32).pin_memory()
     q_stage = torch.empty_like(q_d)
 
     def e2e_step():
         q_stage.copy_(q_host, non_blocking=True)
-        fs.fs_recommend(db, q_stage, k, workspace=ws, l_max=l_max, **outs)
+        fs.fs_recommend(db, q_stage, ks, q_seg_off=q_seg_off, workspace=ws, l_max=l_max, **outs)
         idx_h.copy_(outs["idx"], non_blocking=True)
         dist_h.copy_(outs["dist"], non_blocking=True)
         seq_h.copy_(outs["seq_out"], non_blocking=True)
@@ -318,16 +374,18 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e = {"value": world * pairs * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": Q * F * 4,
-           "d2h_bytes_per_step": Q * k * (4 + 4 + 4 + 2 * l_max),
+           "d2h_bytes_per_step": Q * k_max * (4 + 4 + 4 + 2 * l_max),
            "ms_per_step": e2e_s * 1e3 / args.steps}
 
     # the plain FP32 scan on the same workload, for the "vs plain FP32" ratio
     vs_fp32 = None
     if prec != "fp32" and not args.no_fp32_compare:
         db32, ws32 = make_db("fp32")
-        t32, per32, _, _ = timed(db32, ws32, max(3, args.steps // 4), 2)
-        v32 = pairs * len(per32) / (t32 / 1e3)
-        vs_fp32 = {"fp32_pairs_per_s": v32, "speedup": (pairs * args.steps / (total_ms / 1e3)) / v32}
+        n32 = max(3, args.steps // 4)
+        t32, per32, _, _, _ = timed(db32, ws32, n32, 2, graph=use_graph)
+        v32 = pairs * n32 / (t32 / 1e3)
+        vs_fp32 = {"fp32_pairs_per_s": v32, "fp32_ms_per_step": t32 / n32,
+                   "speedup": (pairs * args.steps / (total_ms / 1e3)) / v32}
         db32.close()
 
     line = {
@@ -338,30 +396,36 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": prec,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "cuda_graph": bool(use_graph),
                    "l2": f"inputs larger than L2 (database {N * F * (4 if prec == 'fp32' else 2 if prec == 'bf16' else 1) / 1e6:.0f} MB scanned per step)"},
         "queries_per_s": world * Q * args.steps / (total_ms / 1e3),
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-        "clocks": clocks, "e2e": e2e, "gpu_launches": prof["launches"],
+        "clocks": clocks, "e2e": e2e, "gpu_launches": int(round(lps * args.steps)),
         "roofline": roof, "vs_fp32_scan": vs_fp32,
-        "stats": st,
+        "stats": st, "db_build_s": build_s,
     }
 
     # CPU oracle on a bounded sample (rank 0, one GPU only), and recall of
     # the GPU answers on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pick, (i_o, d_o, s_o, l_o), dt = oracle_sample(w, args.cpu_sample)
+        pick, ores, dt, spairs = oracle_sample(w, args.cpu_sample)
         step(db, ws, q_d)
         torch.cuda.synchronize()
-        ig = outs["idx"].cpu().numpy()[pick]
-        sg = outs["seq_out"].cpu().numpy()[pick]
-        hit = np.mean([len(set(ig[r]) & set(i_o[r])) / k for r in range(len(pick))])
+        ig = outs["idx"].cpu().numpy()
+        sg = outs["seq_out"].cpu().numpy()
+        seg_of_q, _, _, kk = segment_arrays(w)
+        hits, exact = [], True
+        for q in pick:
+            kq = int(kk[seg_of_q[q]])
+            i_o, d_o, s_o, l_o = ores[int(q)]
+            hits.append(len(set(ig[q, :kq]) & set(i_o[:kq])) / kq)
+            exact &= bool(np.array_equal(ig[q, :kq], i_o[:kq]) and np.array_equal(sg[q, :kq], s_o[:kq]))
         line["cpu_baseline"] = {
-            "value": len(pick) * N / dt, "unit": UNIT, "cores": _NCPU, "kind": "oracle",
-            "sample": f"{len(pick)} of {Q:,} queries against all {N:,} rows",
+            "value": spairs / dt, "unit": UNIT, "cores": _NCPU, "kind": "oracle",
+            "sample": f"{len(pick)} of {Q:,} queries, each against its whole database",
             "seconds": dt, "queries_per_s": len(pick) / dt,
-            "sample_recall": float(hit),
-            "sample_exact": bool(np.array_equal(ig, i_o) and np.array_equal(sg, s_o))}
-        line["recall"] = float(hit)
+            "sample_recall": float(np.mean(hits)), "sample_exact": exact}
+        line["recall"] = float(np.mean(hits))
     db.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -376,12 +440,18 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="fp32_scale", choices=sorted(fsgen.CONFIGS))
+    ap.add_argument("--workload", default="fp32_scale", choices=sorted(fsgen.CONFIGS) + ["batching"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--n", type=int, default=None,
+                    help="database rows instead of the workload's (bounded profiling cases)")
+    ap.add_argument("--q", type=int, default=None, help="queries instead of the workload's")
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--graph", dest="graph", action="store_true", default=None,
+                    help="replay each step as a captured CUDA graph (default: segmented workloads)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")

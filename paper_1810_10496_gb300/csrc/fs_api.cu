@@ -22,6 +22,7 @@ using namespace fsk;
 struct fs_db {
     int dev = 0;
     int num_sms = 0;
+    int64_t l2_bytes = 0;
     int64_t n = 0;
     int32_t f = 0, fu = 0, fl = 0;
     fs_precision prec = FS_FP32;
@@ -194,7 +195,8 @@ Bounds score_bounds(const fs_db* db, double r_xmax) {
 // planning of one search call
 
 struct Plan {
-    std::vector<SegPlan> seg;
+    std::vector<SegPlan> seg;       // scan-item order: largest work first
+    std::vector<int32_t> q_order;   // indices into seg sorted by first query
     int64_t total_items = 0;
     int64_t total_cand = 0;
     int k_max = 0;
@@ -204,7 +206,7 @@ struct Plan {
 };
 
 struct Layout {
-    size_t plan, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
+    size_t plan, q_order, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
         fb_score, fb_index, shared_thr, total;
 };
 
@@ -251,27 +253,75 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
     }
     // the tensor-core scan keeps 8-entry lists when every k fits (fewer inserts)
     pl.list_t = (tensor_scan(db) && !sizing && pl.k_max <= kListTSmall) ? kListTSmall : kListT;
+    // Row chunking. (1) Items of about work / (4 slots) tiles keep every block
+    // busy. (2) Blocks that run at the same time scan about slots / qtiles + 1
+    // chunks of a segment; those chunks should fit in half of L2 so the query
+    // tiles of a chunk read its rows from L2, not HBM. (3) Among chunk counts
+    // meeting (1) and (2), take the one that fills the last round of items
+    // best (blocks take items round robin).
     const int64_t desired = (int64_t)pl.slots * 4;
     const int64_t tiles_per_item = std::max<int64_t>(1, ceil_div(work, desired));
-    int64_t item = 0, cand = 0;
+    const int64_t row_bytes = tensor_scan(db) ? (int64_t)db->fl * (db->prec == FS_BF16 ? 2 : 1)
+                                              : (int64_t)db->fu * 4;
+    const int64_t l2_bytes = std::max<int64_t>(db->l2_bytes, 32 << 20);
+    std::vector<int64_t> seg_work(n_seg, 0);
     for (int s = 0; s < n_seg; ++s) {
         SegPlan& p = pl.seg[s];
         const int64_t row_tiles = ceil_div(p.nrows, pl.tile_rows);
-        const int64_t chunk_tiles = std::max<int64_t>(1, std::min(row_tiles, tiles_per_item));
+        int64_t chunk_tiles = std::max<int64_t>(1, std::min(row_tiles, tiles_per_item));
+        const double live = (double)pl.slots / std::max(1, p.qtiles) + 1.0;
+        if (n_seg == 1 && p.qtiles >= 2 && row_tiles > 1 &&
+            live * chunk_tiles * pl.tile_rows * row_bytes > (double)l2_bytes) {
+            // the chunks in flight overflow L2: cap them at half of it
+            const int64_t cap = std::max<int64_t>(
+                1, (int64_t)(l2_bytes / 2 / (live * row_bytes * pl.tile_rows)));
+            int64_t c_lo = ceil_div(row_tiles, std::min(chunk_tiles, cap));
+            double best = -1.0;
+            int64_t best_c = c_lo;
+            for (int64_t c = c_lo; c <= std::min(row_tiles, c_lo + 64); ++c) {
+                const int64_t items = c * p.qtiles;
+                const double fill = (double)items / (double)(ceil_div(items, pl.slots) * pl.slots);
+                if (fill > best + 1e-3) {
+                    best = fill;
+                    best_c = c;
+                }
+                if (fill > 0.985) break;
+            }
+            chunk_tiles = ceil_div(row_tiles, best_c);
+        }
         p.chunk_rows = (int32_t)(chunk_tiles * pl.tile_rows);
         p.chunks = p.nrows > 0 ? (int32_t)ceil_div(p.nrows, p.chunk_rows) : 0;
-        p.item0 = item;
-        p.cand0 = cand;
         p.list_t = pl.list_t;
-        if (p.nq > 0 && p.nrows > 0) {
-            item += (int64_t)p.qtiles * p.chunks;
-            cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
-        }
         const Bounds b = score_bounds(db, db->r_max[s]);
         p.bound_scan = (float)b.scan;
         p.bound_rq = (float)b.rq;
         p.bound_rerank = (float)b.rerank;
+        if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.qtiles * row_tiles;
     }
+    // number the scan items largest segment first: blocks take items round
+    // robin, so the long ones start first and the short ones fill in
+    std::vector<int32_t> order(n_seg);
+    for (int s = 0; s < n_seg; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return seg_work[a] > seg_work[b]; });
+    std::vector<SegPlan> sorted(n_seg);
+    std::vector<int32_t> pos_of(n_seg);
+    int64_t item = 0, cand = 0;
+    for (int i = 0; i < n_seg; ++i) {
+        SegPlan p = pl.seg[order[i]];
+        p.item0 = item;
+        p.cand0 = cand;
+        if (p.nq > 0 && p.nrows > 0) {
+            item += (int64_t)p.qtiles * p.chunks;
+            cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
+        }
+        sorted[i] = p;
+        pos_of[order[i]] = i;
+    }
+    pl.seg.swap(sorted);
+    // the segments in their original (first-query) order
+    pl.q_order.resize(n_seg);
+    for (int s = 0; s < n_seg; ++s) pl.q_order[s] = pos_of[s];
     pl.total_items = item;
     pl.total_cand = cand;
     return FS_OK;
@@ -287,6 +337,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     };
     const size_t lw = db->prec == FS_BF16 ? 2 : 1;
     L.plan = take(sizeof(SegPlan) * pl.seg.size());
+    L.q_order = take(sizeof(int32_t) * pl.seg.size());
     L.q_a64 = take(sizeof(double) * nq);
     L.q_ss = take(sizeof(float) * nq);
     L.q_unit = take(sizeof(float) * (size_t)nq * db->fu);
@@ -360,6 +411,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     CallView c;
     std::memset(&c, 0, sizeof(c));
     c.plan = (const SegPlan*)(ws + L.plan);
+    c.q_order = (const int32_t*)(ws + L.q_order);
     c.q_raw = q;
     c.q_a64 = (double*)(ws + L.q_a64);
     c.q_ss = (float*)(ws + L.q_ss);
@@ -385,7 +437,8 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
 
     {
         StageTimer t(FS_STAGE_PREPARE, cs);
-        FS_CUDA(launch_write_plan(pl.seg.data(), db->n_seg, (SegPlan*)(ws + L.plan), c.fb_count,
+        FS_CUDA(launch_write_plan(pl.seg.data(), pl.q_order.data(), db->n_seg,
+                                  (SegPlan*)(ws + L.plan), (int32_t*)(ws + L.q_order), c.fb_count,
                                   c.work_counter, cs));
         FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_ss, c.q_lowp, db->fl,
                                     c.q_scale, c.q_resid, db->prec, db->status, cs));
@@ -505,6 +558,11 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
 
     FS_TRY_CUDA(cudaGetDevice(&db->dev));
     FS_TRY_CUDA(cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->dev));
+    {
+        int l2 = 0;
+        FS_TRY_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, db->dev));
+        db->l2_bytes = l2;
+    }
     db->n = n;
     db->f = f;
     db->fu = (int)round_up(f, 32);

@@ -100,7 +100,8 @@ struct DbView {
 };
 
 struct CallView {
-    const SegPlan* plan;      // [n_seg], in query order
+    const SegPlan* plan;      // [n_seg], in scan-item order (largest work first)
+    const int32_t* q_order;   // [n_seg] plan indices sorted by first query
     const float* q_raw;       // [nq][f] caller's queries
     double* q_a64;            // [nq] binary64 sum of squares (queries sent to the fallback)
     float* q_ss;              // [nq] FP32 sum of squares (0 exactly for a zero query)
@@ -114,8 +115,8 @@ struct CallView {
     double* fb_score;         // [nq][kFbChunks][FS_MAX_K]
     int32_t* fb_index;        // [nq][kFbChunks][FS_MAX_K]
     int32_t* work_counter;    // dynamic scan scheduler
-    uint32_t* shared_thr;     // [nq] per query: highest lowest-kept score of any
-                              // full candidate list so far (order-mapped bits)
+    uint32_t* shared_thr;     // [nq] per query: a score below which no row can be
+                              // among the k nearest (order-mapped bits)
     const int32_t* exclude;   // [nq] or NULL
     int32_t* out_idx;         // [nq][k_max]
     float* out_dist;          // [nq][k_max]
@@ -141,8 +142,9 @@ cudaError_t launch_segment_max(const float* v, const int64_t* seg_off_dev, int n
                                float* out, cudaStream_t st);
 
 // select.cu
-cudaError_t launch_write_plan(const SegPlan* host_plan, int n_seg, SegPlan* dev_plan,
-                              int32_t* fb_count, int32_t* work_counter, cudaStream_t st);
+cudaError_t launch_write_plan(const SegPlan* host_plan, const int32_t* host_q_order, int n_seg,
+                              SegPlan* dev_plan, int32_t* dev_q_order, int32_t* fb_count,
+                              int32_t* work_counter, cudaStream_t st);
 cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st);
 cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
                             cudaStream_t st);
@@ -163,7 +165,8 @@ int scan_fp32_ctas_per_sm();
 constexpr int kTcTileRows = 256;
 constexpr int kTcQueryRows = 128;
 constexpr int kTcLists = 2;        // candidate lists per (query, chunk): tile halves
-size_t scan_tc_smem_bytes();
+size_t scan_tc_smem_bytes(int kblocks, int stages);
+int scan_tc_stages(int kblocks, bool fp8);
 cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols,
                           int elem_bytes, int box_rows);
 cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,

@@ -8,18 +8,20 @@
 // 5th-generation tensor cores and filters without ever writing it out:
 //
 //   * A = 128 queries (K-major, resident in shared memory for a work item),
-//     B = 256 database rows per tile (K-major, streamed by TMA through a
-//     4-stage ring of 128-byte-swizzled K blocks), D = 128 x 256 FP32 scores
-//     in tensor memory, double buffered (2 x 256 of the 512 columns) so the
-//     epilogue of one tile overlaps the MMAs of the next.
+//     B = 256 database rows per tile (K-major, streamed by TMA through a ring
+//     of 128-byte-swizzled K blocks of 32 KB, as deep as shared memory
+//     allows), D = 128 x 256 FP32 scores in tensor memory, two accumulators
+//     (all 512 columns) so the epilogue of one tile overlaps the MMAs of the
+//     next.
 //   * Warp 0 issues the TMA loads, warp 1 (one thread) issues tcgen05.mma,
 //     warps 2-9 are the epilogue, two per TMEM lane quarter: a thread owns
 //     one query of the tile (its TMEM lane) and one half of each tile's 256
 //     columns, reads its 128 scores with tcgen05.ld and keeps its 8 or 16
 //     best (score, row) pairs in registers, tested against a running
-//     threshold with one max per 64 scores in the common case. A block
-//     also drops rows below the best threshold any block has published for
-//     the query; lanes with candidates insert them together.
+//     threshold with one max per 64 scores in the common case. Blocks share
+//     per query the k-th best score seen so far minus twice the error bound,
+//     below which no row can reach the top k; lanes with candidates insert
+//     them together.
 //   * FP8 scores are acc * s_row * s_query (per-vector scales, Sec. 4.2's
 //     cosine of the dequantised vectors); BF16 scores are acc itself.
 //
@@ -46,21 +48,22 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 64 + kEpiThreads;  // + TMA warp + MMA warp
 constexpr int BM = 128;                     // queries per tile (MMA M)
 constexpr int BN = kTcTileRows;             // database rows per tile (MMA N)
-constexpr int kStages = 4;
+constexpr int kMaxStages = 16;              // ring slots (as many as shared memory holds)
 constexpr uint32_t kStageBytes = BN * 128;  // one 128-byte K block of BN rows
 constexpr uint32_t kABlockBytes = BM * 128; // one 128-byte K block of BM queries
 constexpr int kMaxKBlocks = 4;              // 256 BF16 or 512 FP8 features
-constexpr uint32_t kTmemCols = 2 * BN;
+constexpr int kAccs = 512 / BN;              // accumulators in tensor memory
+constexpr uint32_t kTmemCols = kAccs * BN;
 
 struct Bars {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
-    uint64_t tmem_full[2];
-    uint64_t tmem_empty[2];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t tmem_full[kAccs];
+    uint64_t tmem_empty[kAccs];
     uint64_t a_full;
     uint64_t a_empty;
     uint64_t drain;
-    uint64_t sx_ready[2];   // FP8: the tile's row scales are staged
+    uint64_t sx_ready[kAccs];   // FP8: the tile's row scales are staged
 };
 
 __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
@@ -134,6 +137,20 @@ struct RegList {
         thr_s = key_score(m[0]);
     }
 
+    // Score of the kk-th best key held (kk <= cnt): kk rounds of a maximum
+    // below the previous one (keys are distinct: each holds its row).
+    __device__ __forceinline__ float kth_score(int kk) const {
+        uint64_t prev = ~0ull, best = 0;
+        for (int r = 0; r < kk; ++r) {
+            best = 0;
+#pragma unroll
+            for (int e = 0; e < LT; ++e)
+                if (k[e] < prev && k[e] > best) best = k[e];
+            prev = best;
+        }
+        return key_score(best);
+    }
+
     // Offers (score, row): kept if the list is filling or it beats the lowest.
     __device__ __forceinline__ void offer(float v, int64_t row, int64_t row_end, int64_t row0,
                                           int excl) {
@@ -155,23 +172,6 @@ struct RegList {
     }
 };
 
-// v[j] for a run-time j in 0..63 by a 6-level select tree (the array stays in
-// registers; a dynamic index would move it to local memory).
-__device__ __forceinline__ float select64(const float (&v)[64], int j) {
-    float a[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = (j & 1) ? v[2 * i + 1] : v[2 * i];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) a[i] = (j & 2) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = (j & 4) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = (j & 8) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) a[i] = (j & 16) ? a[2 * i + 1] : a[2 * i];
-    return (j & 32) ? a[1] : a[0];
-}
-
 // A bounded wait that ignores the abort flag (used to drain on the way out).
 __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
     const uint64_t t0 = globaltimer();
@@ -182,35 +182,34 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
 template <bool FP8, int LT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
-          const __grid_constant__ CUtensorMap map_x, int kblocks) {
+          const __grid_constant__ CUtensorMap map_x, int kblocks, int stages) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ Bars bars;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
-    __shared__ __align__(16) float sx[2][BN];   // FP8: the tile's row scales, per accumulator
+    __shared__ __align__(16) float sx[kAccs][BN];   // FP8: the tile's row scales, per accumulator
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t a_smem = base;
-    const uint32_t b_smem = a_smem + kMaxKBlocks * kABlockBytes;
+    const uint32_t b_smem = a_smem + kblocks * kABlockBytes;
     constexpr int kElemsPerKBlock = FP8 ? 128 : 64;
-    const uint32_t idesc = FP8 ? kIdescE4m3 : kIdescBf16;
+    const uint32_t idesc = FP8 ? instr_desc(0, BM, BN) : instr_desc(1, BM, BN);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(smem_u32(&bars.full[s]), 1);
             mbar_init(smem_u32(&bars.empty[s]), 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < kAccs; ++a) {
             mbar_init(smem_u32(&bars.tmem_full[a]), 1);
             mbar_init(smem_u32(&bars.tmem_empty[a]), kEpiThreads);
         }
         mbar_init(smem_u32(&bars.a_full), 1);
         mbar_init(smem_u32(&bars.a_empty), 1);
         mbar_init(smem_u32(&bars.drain), 1);
-        mbar_init(smem_u32(&bars.sx_ready[0]), kEpiThreads);
-        mbar_init(smem_u32(&bars.sx_ready[1]), kEpiThreads);
+        for (int a = 0; a < kAccs; ++a) mbar_init(smem_u32(&bars.sx_ready[a]), kEpiThreads);
         fence_barrier_init();
     }
     if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), kTmemCols);
@@ -239,7 +238,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 for (int t = 0; ok && t < w.ntiles; ++t) {
                     const int32_t row = (int32_t)(w.row_begin + (int64_t)t * BN);
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
-                        const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+                        const uint32_t s = it % stages, ph = (it / stages) & 1;
                         ok = mbar_wait(smem_u32(&bars.empty[s]), ph ^ 1, &abort_flag);
                         if (!ok) break;
                         mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kStageBytes);
@@ -250,8 +249,8 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             }
             if (!ok) {
                 // let the copies already issued land before the block exits
-                for (uint32_t j = (it >= kStages ? it - kStages : 0); j < it; ++j)
-                    drain_wait(smem_u32(&bars.full[j % kStages]), (j / kStages) & 1);
+                for (uint32_t j = (it >= (uint32_t)stages ? it - stages : 0); j < it; ++j)
+                    drain_wait(smem_u32(&bars.full[j % stages]), (j / stages) & 1);
                 if (a_loads > 0) drain_wait(smem_u32(&bars.a_full), (a_loads - 1) & 1);
             }
         }
@@ -267,13 +266,13 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (!ok) break;
                 tc_fence_after();
                 for (int t = 0; ok && t < w.ntiles; ++t, ++tcount) {
-                    const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                    const uint32_t acc = tcount % kAccs, aph = (tcount / kAccs) & 1;
                     ok = mbar_wait(smem_u32(&bars.tmem_empty[acc]), aph ^ 1, &abort_flag);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d = tmem_base + acc * BN;
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
-                        const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+                        const uint32_t s = it % stages, ph = (it / stages) & 1;
                         ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
                         if (!ok) break;
                         tc_fence_after();
@@ -316,20 +315,26 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             st.reset();
 
             float published = -INFINITY;
-            // the best lowest-kept score any full list of this query reached (any
-            // block); rows below it cannot reach the top k. It is read one tile
-            // ahead so the L2 round trip overlaps the current tile.
+            // Pruning bound shared by every block scanning this query: the k-th
+            // best approximate score any block has seen, minus twice the score
+            // error bound E. A row scoring below it is at least 2E under k rows'
+            // scores, so its cosine is below theirs: it cannot be among the k
+            // nearest, and dropping it never affects certification. Read one
+            // tile ahead so the L2 round trip overlaps the current tile.
+            const float e2 =
+                qvalid ? 2.0f * (w.p.bound_scan + w.p.bound_rq * call.q_resid[w.qbase + lq]) * 1.0001f
+                       : 0.0f;
             const uint32_t* shared_p = call.shared_thr + w.qbase + lq;
             uint32_t shared_next = qvalid ? __ldcg(shared_p) : 0xffffffffu;
             for (int t = 0; t < w.ntiles; ++t, ++tcount) {
-                const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                const uint32_t acc = tcount % kAccs, aph = (tcount / kAccs) & 1;
                 const int64_t tile_row0 = w.row_begin + (int64_t)t * BN;
                 const float shared_s = qvalid ? unord_f32(shared_next) : INFINITY;
                 if (qvalid && t + 1 < w.ntiles) shared_next = __ldcg(shared_p);
                 if (FP8) {
                     // stage the tile's row scales (rows past the data read as 0); every
-                    // epilogue thread finished tile t-2, the last user of sx[acc], before
-                    // any thread could complete the phase of tile t-1
+                    // epilogue thread finished tile t-kAccs, the last user of sx[acc],
+                    // before any thread could complete the phase of the tile after it
                     for (int j = et; j < BN; j += kEpiThreads) {
                         const int64_t r = tile_row0 + j;
                         sx[acc][j] = r < w.row_end ? db.scale[r] : 0.0f;
@@ -373,8 +378,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                           fmaxf(fmaxf(gm[4], gm[5]), fmaxf(gm[6], gm[7])));
                     float thr = fmaxf(st.thr_s, shared_s);
                     if (__any_sync(0xffffffffu, m >= thr)) {
-                        // this lane's passing columns, only in groups some lane passes
-                        uint64_t mask = 0;
+                        // group by group, with the threshold as it stands (a list that
+                        // is filling tightens after every group): each lane collects
+                        // its passing columns of the group, then every lane takes its
+                        // next candidate in the same round
 #pragma unroll
                         for (int g = 0; g < 8; ++g) {
                             if (__any_sync(0xffffffffu, gm[g] >= thr)) {
@@ -384,18 +391,24 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                     const float sc = FP8 ? v[8 * g + i] * sq : v[8 * g + i];
                                     bits |= (sc >= thr ? 1u : 0u) << i;
                                 }
-                                mask |= (uint64_t)bits << (8 * g);
-                            }
-                        }
-                        // every lane takes its next candidate in the same iteration
-                        while (__any_sync(0xffffffffu, mask != 0)) {
-                            if (mask != 0) {
-                                const int j = __ffsll((long long)mask) - 1;
-                                mask &= mask - 1;
-                                const float sc = FP8 ? select64(v, j) * sq : select64(v, j);
-                                if (sc >= thr) {
-                                    st.offer(sc, tile_row0 + c0 + j, w.row_end, w.p.row0, excl);
-                                    thr = fmaxf(st.thr_s, shared_s);
+                                while (__any_sync(0xffffffffu, bits != 0)) {
+                                    if (bits != 0) {
+                                        const int i = __ffs(bits) - 1;
+                                        bits &= bits - 1;
+                                        const float a0 = (i & 1) ? v[8 * g + 1] : v[8 * g];
+                                        const float a1 = (i & 1) ? v[8 * g + 3] : v[8 * g + 2];
+                                        const float a2 = (i & 1) ? v[8 * g + 5] : v[8 * g + 4];
+                                        const float a3 = (i & 1) ? v[8 * g + 7] : v[8 * g + 6];
+                                        const float b0 = (i & 2) ? a1 : a0;
+                                        const float b1 = (i & 2) ? a3 : a2;
+                                        const float raw = (i & 4) ? b1 : b0;
+                                        const float sc = FP8 ? raw * sq : raw;
+                                        if (sc >= thr) {
+                                            st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
+                                                     w.p.row0, excl);
+                                            thr = fmaxf(st.thr_s, shared_s);
+                                        }
+                                    }
                                 }
                             }
                         }
@@ -404,9 +417,14 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bars.tmem_empty[acc]));
-                if (qvalid && st.cnt == LT && st.thr_s > published) {
-                    atomicMax(call.shared_thr + w.qbase + lq, ord_f32(st.thr_s));
-                    published = st.thr_s;
+                if (qvalid && st.cnt >= w.p.k) {
+                    const float kth = st.kth_score(w.p.k);
+                    // rounded down: the bound may only err low
+                    const float bound = (kth - e2) - fabsf(kth) * 0x1p-20f;
+                    if (bound > published) {
+                        atomicMax(call.shared_thr + w.qbase + lq, ord_f32(bound));
+                        published = bound;
+                    }
                 }
             }
             if (ok && qvalid) {
@@ -443,8 +461,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t scan_tc_smem_bytes() {
-    return 1024 + kMaxKBlocks * kABlockBytes + kStages * kStageBytes;
+// Dynamic shared memory of a launch: the alignment slack, the query tile
+// (kblocks K blocks) and `stages` ring slots.
+size_t scan_tc_smem_bytes(int kblocks, int stages) {
+    return 1024 + (size_t)kblocks * kABlockBytes + (size_t)stages * kStageBytes;
+}
+
+// As many ring slots as fit next to the query tile and the static shared
+// memory (barriers, FP8 scale staging), between 2 and kMaxStages.
+int scan_tc_stages(int kblocks, bool fp8) {
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 232448;
+    const size_t static_bytes = sizeof(Bars) + 64 + (fp8 ? kAccs * BN * sizeof(float) : 0);
+    const long avail = (long)optin - (long)static_bytes - 1024 - (long)kblocks * kABlockBytes;
+    int st = (int)(avail / (long)kStageBytes);
+    return st < 2 ? 2 : (st > kMaxStages ? kMaxStages : st);
 }
 
 // 2-D tensor map of a row-major [rows][cols] array of 1- or 2-byte codes,
@@ -467,15 +500,16 @@ cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int c
 template <bool FP8, int LT>
 cudaError_t launch_variant(const DbView& db, const CallView& call, const CUtensorMap& map_q,
                            const CUtensorMap& map_x, int grid, int kblocks, cudaStream_t st) {
-    static bool attr_set = false;
-    const size_t smem = scan_tc_smem_bytes();
-    if (!attr_set) {
+    static size_t attr_bytes = 0;   // the largest dynamic size set so far
+    const int stages = scan_tc_stages(kblocks, FP8);
+    const size_t smem = scan_tc_smem_bytes(kblocks, stages);
+    if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(k_scan_tc<FP8, LT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_bytes = smem;
     }
-    k_scan_tc<FP8, LT><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks);
+    k_scan_tc<FP8, LT><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks, stages);
     return cudaGetLastError();
 }
 

@@ -10,10 +10,11 @@
 //     approximate score t_k.
 //  2. Certify: every approximate score is within E of the true cosine. A
 //     list that filled up dropped rows scoring at most its lowest kept score
-//     tau (rows below a score another full list published were dropped too,
-//     and such a score never exceeds that list's final tau); if tau + 2E <
-//     t_k for every full list, no dropped row can be among the k nearest.
-//     Otherwise the query goes to the exact fallback scan.
+//     tau; if tau + 2E < t_k for every full list, no dropped row can be among
+//     the k nearest. (The tensor-core scan also drops rows scoring below a
+//     shared bound, the k-th best score seen minus 2E: such a row is provably
+//     not among the k nearest, so it needs no certificate.) Otherwise the
+//     query goes to the exact fallback scan.
 //  3. Window: only candidates with approximate score >= t_k - 2E can be in
 //     the top k (at most 64 are taken; more also sends the query to the
 //     fallback).
@@ -37,25 +38,31 @@ constexpr int kPlanPerLaunch = 256;
 
 struct PlanChunk {
     SegPlan p[kPlanPerLaunch];
+    int32_t q_order[kPlanPerLaunch];
 };
 
-__global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* fb_count,
-                             int32_t* work_counter) {
+__global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* dst_q_order,
+                             int32_t* fb_count, int32_t* work_counter) {
     int i = threadIdx.x;
-    if (i < n) dst[i] = chunk.p[i];
+    if (i < n) {
+        dst[i] = chunk.p[i];
+        dst_q_order[i] = chunk.q_order[i];
+    }
     if (i == 0 && fb_count) {
         *fb_count = 0;
         *work_counter = 0;
     }
 }
 
-__device__ __forceinline__ int plan_of_query(const SegPlan* plan, int n_seg, int q) {
-    int lo = 0, hi = n_seg - 1;
+// The plan entry of query q: the last entry, in first-query order, whose
+// first query is <= q (segments without queries precede the one that owns q).
+__device__ __forceinline__ int plan_of_query(const CallView& call, int q) {
+    int lo = 0, hi = call.n_seg - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (plan[mid].q0 <= q) lo = mid; else hi = mid - 1;
+        if (call.plan[call.q_order[mid]].q0 <= q) lo = mid; else hi = mid - 1;
     }
-    return lo;
+    return call.q_order[lo];
 }
 
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
@@ -156,7 +163,7 @@ k_select(DbView db, CallView call) {
     const int q = blockIdx.x * kSelWarps + wid;
 
     if (q < call.nq) {
-        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const SegPlan p = call.plan[plan_of_query(call, q)];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
         const int excl = call.exclude ? call.exclude[q] : -1;
@@ -377,7 +384,7 @@ k_fallback_scan(DbView db, CallView call) {
     for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
         const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
         const int q = call.fb_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const SegPlan p = call.plan[plan_of_query(call, q)];
         const int k = p.k;
         const int excl = call.exclude ? call.exclude[q] : -1;
         const double a64 = call.q_a64[q];
@@ -444,7 +451,7 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
     const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (slot < nfb) {
         const int q = call.fb_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+        const SegPlan p = call.plan[plan_of_query(call, q)];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
         // lane c < kFbChunks owns chunk c's sorted list
@@ -491,7 +498,7 @@ __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= (int64_t)call.nq * call.k_max) return;
     const int q = (int)(w / call.k_max), c = (int)(w % call.k_max);
-    const SegPlan p = call.plan[plan_of_query(call.plan, call.n_seg, q)];
+    const SegPlan p = call.plan[plan_of_query(call, q)];
     const int r = call.out_idx[w];
     int16_t* dst = seq_out + w * l_max;
     int64_t lo = 0, len = 0;
@@ -523,13 +530,17 @@ __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out
 
 }  // namespace
 
-cudaError_t launch_write_plan(const SegPlan* host_plan, int n_seg, SegPlan* dev_plan,
-                              int32_t* fb_count, int32_t* work_counter, cudaStream_t st) {
+cudaError_t launch_write_plan(const SegPlan* host_plan, const int32_t* host_q_order, int n_seg,
+                              SegPlan* dev_plan, int32_t* dev_q_order, int32_t* fb_count,
+                              int32_t* work_counter, cudaStream_t st) {
     for (int base = 0; base < n_seg; base += kPlanPerLaunch) {
         PlanChunk chunk;
         const int n = (n_seg - base) < kPlanPerLaunch ? (n_seg - base) : kPlanPerLaunch;
-        for (int i = 0; i < n; ++i) chunk.p[i] = host_plan[base + i];
-        k_write_plan<<<1, kPlanPerLaunch, 0, st>>>(chunk, n, dev_plan + base,
+        for (int i = 0; i < n; ++i) {
+            chunk.p[i] = host_plan[base + i];
+            chunk.q_order[i] = host_q_order[base + i];
+        }
+        k_write_plan<<<1, kPlanPerLaunch, 0, st>>>(chunk, n, dev_plan + base, dev_q_order + base,
                                                    base == 0 ? fb_count : nullptr, work_counter);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
