@@ -207,7 +207,7 @@ struct Plan {
 
 struct Layout {
     size_t plan, q_order, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
-        fb_score, fb_index, shared_thr, total;
+        fb2_list, cand_fb, fb_score, fb_index, shared_thr, total;
 };
 
 bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
@@ -345,8 +345,10 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.q_scale = take(sizeof(float) * nq);
     L.q_resid = take(sizeof(float) * nq);
     L.cand = take(sizeof(uint64_t) * (size_t)pl.total_cand);
-    L.counters = take(2 * sizeof(int32_t));
+    L.counters = take(4 * sizeof(int32_t));
     L.fb_list = take(sizeof(int32_t) * nq);
+    L.fb2_list = take(sizeof(int32_t) * nq);
+    L.cand_fb = take(sizeof(uint64_t) * (size_t)nq * kFbChunks * kListT);
     L.fb_score = take(sizeof(double) * (size_t)nq * kFbChunks * FS_MAX_K);
     L.fb_index = take(sizeof(int32_t) * (size_t)nq * kFbChunks * FS_MAX_K);
     L.shared_thr = take(sizeof(uint32_t) * nq);
@@ -422,7 +424,10 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.cand = (uint64_t*)(ws + L.cand);
     c.fb_count = (int32_t*)(ws + L.counters);
     c.work_counter = c.fb_count + 1;
+    c.fb2_count = c.fb_count + 2;
     c.fb_list = (int32_t*)(ws + L.fb_list);
+    c.fb2_list = (int32_t*)(ws + L.fb2_list);
+    c.cand_fb = (uint64_t*)(ws + L.cand_fb);
     c.fb_score = (double*)(ws + L.fb_score);
     c.fb_index = (int32_t*)(ws + L.fb_index);
     c.shared_thr = (uint32_t*)(ws + L.shared_thr);
@@ -468,7 +473,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     {
         StageTimer t(FS_STAGE_FALLBACK, cs);
         FS_CUDA(launch_fallback(v, c, db->num_sms, cs));
-        t.finish(2);
+        t.finish(4);
     }
     if (gather) {
         StageTimer t(FS_STAGE_GATHER, cs);

@@ -95,83 +95,6 @@ __device__ __forceinline__ Item decode(const CallView& call, int64_t item) {
     return it;
 }
 
-// One thread's candidate list, held in registers: LT keys (every index is a
-// compile-time constant, so the array never leaves the register file).
-template <int LT>
-struct RegList {
-    uint64_t k[LT];
-    uint64_t thr_key;  // lowest key kept once the list is full (0 before)
-    float thr_s;       // its score; -inf while the list is filling
-    int cnt;           // keys stored so far
-    int min_slot;      // slot of thr_key
-
-    __device__ __forceinline__ void reset() {
-#pragma unroll
-        for (int e = 0; e < LT; ++e) k[e] = 0;
-        thr_key = 0;
-        thr_s = -INFINITY;
-        cnt = 0;
-        min_slot = 0;
-    }
-
-    // new minimum: a tree over the slots
-    __device__ __forceinline__ void recompute() {
-        uint64_t m[LT];
-        int slot[LT];
-#pragma unroll
-        for (int e = 0; e < LT; ++e) {
-            m[e] = k[e];
-            slot[e] = e;
-        }
-#pragma unroll
-        for (int w = LT / 2; w > 0; w >>= 1) {
-#pragma unroll
-            for (int e = 0; e < w; ++e) {
-                const bool lo = m[e + w] < m[e];
-                m[e] = lo ? m[e + w] : m[e];
-                slot[e] = lo ? slot[e + w] : slot[e];
-            }
-        }
-        thr_key = m[0];
-        min_slot = slot[0];
-        thr_s = key_score(m[0]);
-    }
-
-    // Score of the kk-th best key held (kk <= cnt): kk rounds of a maximum
-    // below the previous one (keys are distinct: each holds its row).
-    __device__ __forceinline__ float kth_score(int kk) const {
-        uint64_t prev = ~0ull, best = 0;
-        for (int r = 0; r < kk; ++r) {
-            best = 0;
-#pragma unroll
-            for (int e = 0; e < LT; ++e)
-                if (k[e] < prev && k[e] > best) best = k[e];
-            prev = best;
-        }
-        return key_score(best);
-    }
-
-    // Offers (score, row): kept if the list is filling or it beats the lowest.
-    __device__ __forceinline__ void offer(float v, int64_t row, int64_t row_end, int64_t row0,
-                                          int excl) {
-        const int32_t li = (int32_t)(row - row0);
-        if (row >= row_end || li == excl) return;
-        const uint64_t key = make_key(v, (uint32_t)li);
-        int at;
-        if (cnt < LT) {
-            at = cnt++;
-        } else if (key > thr_key) {
-            at = min_slot;
-        } else {
-            return;
-        }
-#pragma unroll
-        for (int e = 0; e < LT; ++e)
-            if (e == at) k[e] = key;
-        if (cnt == LT) recompute();
-    }
-};
-
 // A bounded wait that ignores the abort flag (used to drain on the way out).
 __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
     const uint64_t t0 = globaltimer();

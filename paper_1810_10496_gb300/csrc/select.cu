@@ -49,7 +49,8 @@ __global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* dst_
         dst_q_order[i] = chunk.q_order[i];
     }
     if (i == 0 && fb_count) {
-        *fb_count = 0;
+        fb_count[0] = 0;    // queries for the FP32 rescan
+        fb_count[2] = 0;    // queries for the binary64 scan
         *work_counter = 0;
     }
 }
@@ -154,6 +155,175 @@ __device__ double exact_norm2(const float* __restrict__ q, int f) {
     return a;
 }
 
+// Answers query q from its candidate lists: cand holds nl lists of lt keys,
+// every approximate score within E of the exact cosine. Returns the number of
+// places written, or -1 when the lists do not certify the answer (nothing is
+// written then). Whole warp.
+__device__ int answer_from_lists(const DbView& db, const CallView& call, SelShared& sh, int wid,
+                                 int lane, int q, const SegPlan& p, const uint64_t* cand, int nl,
+                                 int lt, double E, unsigned long long* stats) {
+    const int k = p.k;
+    const int64_t out0 = (int64_t)q * call.k_max;
+    const int64_t ne = (int64_t)nl * lt;
+
+    // 1. k-th best approximate key
+    uint64_t prev = ~0ull, kth = 0;
+    int ntop = 0;
+    for (int r = 0; r < k; ++r) {
+        uint64_t best = 0;
+        for (int64_t e = lane; e < ne; e += 32) {
+            uint64_t v = cand[e];
+            if (v < prev && v > best) best = v;
+        }
+        best = warp_max_u64(best);
+        if (best == 0) break;
+        prev = best;
+        kth = best;
+        ++ntop;
+    }
+
+    // 2. certification against the lowest kept key of every full list
+    uint64_t tau = 0;
+    for (int l = lane; l < nl; l += 32) {
+        uint64_t mn = ~0ull;
+        for (int e = 0; e < lt; ++e) {
+            uint64_t v = cand[(int64_t)l * lt + e];
+            mn = v < mn ? v : mn;
+        }
+        if (mn != 0) tau = mn > tau ? mn : tau;   // full list
+    }
+    tau = warp_max_u64(tau);
+    const double tk = ntop ? (double)key_score(kth) : -INFINITY;
+    bool certified = (tau == 0) || ((double)key_score(tau) + 2.0 * E < tk);
+
+    // 3. window of candidates that can still reach the top k
+    int nw = 0;
+    if (certified && ntop > 0) {
+        const double lo = tk - 2.0 * E;
+        for (int64_t e0 = 0; e0 < ne; e0 += 32) {
+            const int64_t e = e0 + lane;
+            uint64_t v = e < ne ? cand[e] : 0;
+            bool in = v != 0 && (double)key_score(v) >= lo;
+            unsigned m = __ballot_sync(kFull, in);
+            int pos = nw + __popc(m & ((1u << lane) - 1));
+            if (in && pos < kWindow) sh.widx[wid][pos] = key_index(v);
+            nw += __popc(m);
+        }
+        if (nw > kWindow) certified = false;
+    }
+    __syncwarp();
+    if (!certified) return -1;
+
+    // 4. FP32 rescoring of the window: the cosine of the unit vectors and
+    //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
+    const float* qu = call.q_unit + (int64_t)q * db.fu;
+    for (int w = 0; w < nw; ++w) {
+        const int64_t row = p.row0 + sh.widx[wid][w];
+        const float* xu = db.unit + row * (int64_t)db.fu;
+        float dot = 0.0f, dd = 0.0f;
+        for (int i = lane; i < db.fu; i += 32) {
+            const float a = qu[i], b = xu[i];
+            dot = fmaf(a, b, dot);
+            const float t = a - b;
+            dd = fmaf(t, t, dd);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dot += __shfl_xor_sync(kFull, dot, o);
+            dd += __shfl_xor_sync(kFull, dd, o);
+        }
+        if (lane == 0) {
+            sh.wsc[wid][w] = dot;
+            // a zero row has cosine 0 by convention: d = 1
+            sh.wdist[wid][w] = db.b64[row] == 0.0 ? 1.0f : 0.5f * dd;
+        }
+    }
+    __syncwarp();
+    // 5. sort the window by (rescored desc, row asc)
+    for (int w = lane; w < nw; w += 32) {
+        const float sw = sh.wsc[wid][w];
+        const int rw = sh.widx[wid][w];
+        int rank = 0;
+        for (int v = 0; v < nw; ++v) {
+            const float sv = sh.wsc[wid][v];
+            rank += (sv > sw) || (sv == sw && sh.widx[wid][v] < rw);
+        }
+        sh.sidx[wid][rank] = rw;
+        sh.ssc[wid][rank] = sw;
+        sh.sdist[wid][rank] = sh.wdist[wid][w];
+        sh.tie[wid][rank] = 0;
+    }
+    __syncwarp();
+    // 6. near-tie clusters reaching into the first k places: runs whose
+    //    neighbouring rescored values differ by at most 2 E_r
+    int ncl = 0, nfp = 0;
+    if (lane == 0) {
+        const double er2 = 2.0 * (double)p.bound_rerank;
+        int pos = 0;
+        const int lim = min(k, nw);
+        while (pos < lim) {
+            int end = pos + 1;
+            while (end < nw && (double)sh.ssc[wid][end - 1] - (double)sh.ssc[wid][end] <= er2)
+                ++end;
+            if (end - pos >= 2) {
+                sh.cl_begin[wid][ncl] = (int16_t)pos;
+                sh.cl_end[wid][ncl] = (int16_t)end;
+                ++ncl;
+                for (int m = pos; m < end; ++m) sh.tie[wid][m] = 1;
+                nfp += end - pos;
+            }
+            pos = end;
+        }
+    }
+    ncl = __shfl_sync(kFull, ncl, 0);
+    nfp = __shfl_sync(kFull, nfp, 0);
+    __syncwarp();
+    // 7. binary64 scores of the cluster members, one lane each
+    if (ncl > 0) {
+        const float* qr = call.q_raw + (int64_t)q * db.f;
+        for (int m = lane; m < nw; m += 32) {
+            if (sh.tie[wid][m]) {
+                const int64_t row = p.row0 + sh.sidx[wid][m];
+                sh.s64[wid][m] = exact_cosine_ab(qr, db.raw + row * db.f, db.f, db.b64[row]);
+            }
+        }
+        __syncwarp();
+        // order each cluster by (binary64 desc, row asc)
+        if (lane == 0) {
+            for (int c = 0; c < ncl; ++c) {
+                const int b = sh.cl_begin[wid][c], e = sh.cl_end[wid][c];
+                for (int i = b + 1; i < e; ++i) {
+                    const double si = sh.s64[wid][i];
+                    const int ri = sh.sidx[wid][i];
+                    int j = i;
+                    while (j > b && better(si, ri, sh.s64[wid][j - 1], sh.sidx[wid][j - 1])) {
+                        sh.s64[wid][j] = sh.s64[wid][j - 1];
+                        sh.sidx[wid][j] = sh.sidx[wid][j - 1];
+                        --j;
+                    }
+                    sh.s64[wid][j] = si;
+                    sh.sidx[wid][j] = ri;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // 8. the first k places
+    const int nout = min(nw, k);
+    for (int c = lane; c < nout; c += 32) {
+        call.out_idx[out0 + c] = sh.sidx[wid][c];
+        float d = sh.sdist[wid][c];
+        if (sh.tie[wid][c]) d = (float)(1.0 - sh.s64[wid][c]);
+        call.out_dist[out0 + c] = d;
+    }
+    if (lane == 0) {
+        atomicAdd(&stats[kStatRerank], (unsigned long long)nw);
+        atomicAdd(&stats[kStatFp64], (unsigned long long)nfp);
+        atomicAdd(&stats[kStatNearTies], (unsigned long long)ncl);
+    }
+    return nout;
+}
+
 __global__ void __launch_bounds__(kSelWarps * 32)
 k_select(DbView db, CallView call) {
     __shared__ SelShared sh;
@@ -184,184 +354,25 @@ k_select(DbView db, CallView call) {
                 ++c;
             }
             nout = c;
+        } else {
+            const int nl = p.chunks * p.lists;
+            const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * nl * p.list_t;
+            const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
+            nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, nl, p.list_t, E, sh.stats);
+            if (nout < 0 && lane == 0) {
+                // the FP32 rescan of the fallback answers it
+                const int slot = atomicAdd(call.fb_count, 1);
+                call.fb_list[slot] = q;
+                call.q_a64[q] = exact_norm2(call.q_raw + (int64_t)q * db.f, db.f);
+            }
+        }
+        if (nout >= 0) {
+            write_padding(call, q, nout);
             if (lane == 0) {
                 atomicAdd(&sh.stats[kStatQueries], 1ull);
                 atomicAdd(&sh.stats[kStatCertified], 1ull);
             }
-        } else {
-            const int nl = p.chunks * p.lists;
-            const int lt = p.list_t;
-            const int64_t ne = (int64_t)nl * lt;
-            const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * ne;
-
-            // 1. k-th best approximate key
-            uint64_t prev = ~0ull, kth = 0;
-            int ntop = 0;
-            for (int r = 0; r < k; ++r) {
-                uint64_t best = 0;
-                for (int64_t e = lane; e < ne; e += 32) {
-                    uint64_t v = cand[e];
-                    if (v < prev && v > best) best = v;
-                }
-                best = warp_max_u64(best);
-                if (best == 0) break;
-                prev = best;
-                kth = best;
-                ++ntop;
-            }
-
-            // 2. certification against the lowest kept key of every full list
-            uint64_t tau = 0;
-            for (int l = lane; l < nl; l += 32) {
-                uint64_t mn = ~0ull;
-                for (int e = 0; e < lt; ++e) {
-                    uint64_t v = cand[(int64_t)l * lt + e];
-                    mn = v < mn ? v : mn;
-                }
-                if (mn != 0) tau = mn > tau ? mn : tau;   // full list
-            }
-            tau = warp_max_u64(tau);
-            const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
-            const double tk = ntop ? (double)key_score(kth) : -INFINITY;
-            bool certified = (tau == 0) || ((double)key_score(tau) + 2.0 * E < tk);
-
-            // 3. window of candidates that can still reach the top k
-            int nw = 0;
-            if (certified && ntop > 0) {
-                const double lo = tk - 2.0 * E;
-                for (int64_t e0 = 0; e0 < ne; e0 += 32) {
-                    const int64_t e = e0 + lane;
-                    uint64_t v = e < ne ? cand[e] : 0;
-                    bool in = v != 0 && (double)key_score(v) >= lo;
-                    unsigned m = __ballot_sync(kFull, in);
-                    int pos = nw + __popc(m & ((1u << lane) - 1));
-                    if (in && pos < kWindow) sh.widx[wid][pos] = key_index(v);
-                    nw += __popc(m);
-                }
-                if (nw > kWindow) certified = false;
-            }
-            __syncwarp();
-
-            if (!certified) {
-                if (lane == 0) {
-                    int slot = atomicAdd(call.fb_count, 1);
-                    call.fb_list[slot] = q;
-                    call.q_a64[q] = exact_norm2(call.q_raw + (int64_t)q * db.f, db.f);
-                }
-                nout = -1;  // the fallback writes this query
-            } else {
-                // 4. FP32 rescoring of the window: the cosine of the unit vectors and
-                //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
-                const float* qu = call.q_unit + (int64_t)q * db.fu;
-                for (int w = 0; w < nw; ++w) {
-                    const int64_t row = p.row0 + sh.widx[wid][w];
-                    const float* xu = db.unit + row * (int64_t)db.fu;
-                    float dot = 0.0f, dd = 0.0f;
-                    for (int i = lane; i < db.fu; i += 32) {
-                        const float a = qu[i], b = xu[i];
-                        dot = fmaf(a, b, dot);
-                        const float t = a - b;
-                        dd = fmaf(t, t, dd);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        dot += __shfl_xor_sync(kFull, dot, o);
-                        dd += __shfl_xor_sync(kFull, dd, o);
-                    }
-                    if (lane == 0) {
-                        sh.wsc[wid][w] = dot;
-                        // a zero row has cosine 0 by convention: d = 1
-                        sh.wdist[wid][w] = db.b64[row] == 0.0 ? 1.0f : 0.5f * dd;
-                    }
-                }
-                __syncwarp();
-                // 5. sort the window by (rescored desc, row asc)
-                for (int w = lane; w < nw; w += 32) {
-                    const float sw = sh.wsc[wid][w];
-                    const int rw = sh.widx[wid][w];
-                    int rank = 0;
-                    for (int v = 0; v < nw; ++v) {
-                        const float sv = sh.wsc[wid][v];
-                        rank += (sv > sw) || (sv == sw && sh.widx[wid][v] < rw);
-                    }
-                    sh.sidx[wid][rank] = rw;
-                    sh.ssc[wid][rank] = sw;
-                    sh.sdist[wid][rank] = sh.wdist[wid][w];
-                    sh.tie[wid][rank] = 0;
-                }
-                __syncwarp();
-                // 6. near-tie clusters reaching into the first k places: runs whose
-                //    neighbouring rescored values differ by at most 2 E_r
-                int ncl = 0, nfp = 0;
-                if (lane == 0) {
-                    const double er2 = 2.0 * (double)p.bound_rerank;
-                    int pos = 0;
-                    const int lim = min(k, nw);
-                    while (pos < lim) {
-                        int end = pos + 1;
-                        while (end < nw && (double)sh.ssc[wid][end - 1] - (double)sh.ssc[wid][end] <= er2)
-                            ++end;
-                        if (end - pos >= 2) {
-                            sh.cl_begin[wid][ncl] = (int16_t)pos;
-                            sh.cl_end[wid][ncl] = (int16_t)end;
-                            ++ncl;
-                            for (int m = pos; m < end; ++m) sh.tie[wid][m] = 1;
-                            nfp += end - pos;
-                        }
-                        pos = end;
-                    }
-                }
-                ncl = __shfl_sync(kFull, ncl, 0);
-                nfp = __shfl_sync(kFull, nfp, 0);
-                __syncwarp();
-                // 7. binary64 scores of the cluster members, one lane each
-                if (ncl > 0) {
-                    const float* qr = call.q_raw + (int64_t)q * db.f;
-                    for (int m = lane; m < nw; m += 32) {
-                        if (sh.tie[wid][m]) {
-                            const int64_t row = p.row0 + sh.sidx[wid][m];
-                            sh.s64[wid][m] = exact_cosine_ab(qr, db.raw + row * db.f, db.f, db.b64[row]);
-                        }
-                    }
-                    __syncwarp();
-                    // order each cluster by (binary64 desc, row asc)
-                    if (lane == 0) {
-                        for (int c = 0; c < ncl; ++c) {
-                            const int b = sh.cl_begin[wid][c], e = sh.cl_end[wid][c];
-                            for (int i = b + 1; i < e; ++i) {
-                                const double si = sh.s64[wid][i];
-                                const int ri = sh.sidx[wid][i];
-                                int j = i;
-                                while (j > b && better(si, ri, sh.s64[wid][j - 1], sh.sidx[wid][j - 1])) {
-                                    sh.s64[wid][j] = sh.s64[wid][j - 1];
-                                    sh.sidx[wid][j] = sh.sidx[wid][j - 1];
-                                    --j;
-                                }
-                                sh.s64[wid][j] = si;
-                                sh.sidx[wid][j] = ri;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-                // 8. the first k places
-                nout = min(nw, k);
-                for (int c = lane; c < nout; c += 32) {
-                    call.out_idx[out0 + c] = sh.sidx[wid][c];
-                    float d = sh.sdist[wid][c];
-                    if (sh.tie[wid][c]) d = (float)(1.0 - sh.s64[wid][c]);
-                    call.out_dist[out0 + c] = d;
-                }
-                if (lane == 0) {
-                    atomicAdd(&sh.stats[kStatQueries], 1ull);
-                    atomicAdd(&sh.stats[kStatCertified], 1ull);
-                    atomicAdd(&sh.stats[kStatRerank], (unsigned long long)nw);
-                    atomicAdd(&sh.stats[kStatFp64], (unsigned long long)nfp);
-                    atomicAdd(&sh.stats[kStatNearTies], (unsigned long long)ncl);
-                }
-            }
         }
-        if (nout >= 0) write_padding(call, q, nout);
     }
     __syncthreads();
     if (threadIdx.x < kNumStats && sh.stats[threadIdx.x])
@@ -369,21 +380,113 @@ k_select(DbView db, CallView call) {
 }
 
 // ---------------------------------------------------------------------------
-// exact fallback: binary64 scores of every row for the queries that could not
-// be certified, split into kFbChunks row chunks per query
+// first fallback: an FP32 rescan of each uncertified query's database. A warp
+// scores one row at a time with the warp-wide sum of the rerank (error bound
+// E_r, far tighter than a low-precision scan's), keeping the 16 best rows in
+// registers (every lane holds the same list); a block merges its warps into
+// one list per row chunk, and the same certification and selection then run
+// with E = E_r. A query these lists do not certify (more than 16 rows of one
+// chunk within 2 E_r of the k-th best, e.g. many duplicates) goes on to the
+// binary64 scan.
 
 constexpr int kFbThreads = 256;
+constexpr int kFbWarps = kFbThreads / 32;
+
+__global__ void __launch_bounds__(kFbThreads)
+k_fb_scan32(DbView db, CallView call) {
+    __shared__ uint64_t wl[kFbWarps][kListT];
+    const int nfb = *call.fb_count;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
+        const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
+        const int q = call.fb_list[slot];
+        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const int excl = call.exclude ? call.exclude[q] : -1;
+        const int64_t per = ceil_div(p.nrows, kFbChunks);
+        const int64_t lo = p.row0 + chunk * per, hi = p.row0 + min(p.nrows, (int64_t)(chunk + 1) * per);
+        const float* qu = call.q_unit + (int64_t)q * db.fu;
+        RegList<kListT> lst;
+        lst.reset();
+        for (int64_t row = lo + wid; row < hi; row += kFbWarps) {
+            const float* xu = db.unit + row * (int64_t)db.fu;
+            float dot = 0.0f;
+            for (int i = lane; i < db.fu; i += 32) dot = fmaf(qu[i], xu[i], dot);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
+            dot = __shfl_sync(kFull, dot, 0);   // the same value (lane 0's sum) in every lane
+            if (lst.cnt < kListT || dot >= lst.thr_s) lst.offer(dot, row, hi, p.row0, excl);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int e = 0; e < kListT; ++e) wl[wid][e] = lst.k[e];
+        }
+        __syncthreads();
+        if (wid == 0) {
+            // the block's 16 best of the warps' 8 x 16 (rows are distinct)
+            uint64_t mine[kFbWarps * kListT / 32];
+#pragma unroll
+            for (int j = 0; j < kFbWarps * kListT / 32; ++j)
+                mine[j] = (&wl[0][0])[lane + 32 * j];
+            uint64_t prev = ~0ull;
+            uint64_t* dst = call.cand_fb + ((int64_t)slot * kFbChunks + chunk) * kListT;
+            for (int e = 0; e < kListT; ++e) {
+                uint64_t best = 0;
+#pragma unroll
+                for (int j = 0; j < kFbWarps * kListT / 32; ++j)
+                    if (mine[j] < prev && mine[j] > best) best = mine[j];
+                best = warp_max_u64(best);
+                if (lane == 0) dst[e] = best;
+                prev = best;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSelWarps * 32)
+k_fb_select(DbView db, CallView call) {
+    __shared__ SelShared sh;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kNumStats) sh.stats[threadIdx.x] = 0;
+    __syncthreads();
+    const int nfb = *call.fb_count;
+    for (int slot = blockIdx.x * kSelWarps + wid; slot < nfb; slot += gridDim.x * kSelWarps) {
+        const int q = call.fb_list[slot];
+        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const uint64_t* cand = call.cand_fb + (int64_t)slot * kFbChunks * kListT;
+        const int nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, kFbChunks, kListT,
+                                           (double)p.bound_rerank, sh.stats);
+        if (nout >= 0) {
+            write_padding(call, q, nout);
+            if (lane == 0) {
+                atomicAdd(&sh.stats[kStatQueries], 1ull);
+                atomicAdd(&sh.stats[kStatFallback], 1ull);
+            }
+        } else if (lane == 0) {
+            const int s2 = atomicAdd(call.fb2_count, 1);
+            call.fb2_list[s2] = q;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumStats && sh.stats[threadIdx.x])
+        atomicAdd(&db.stats[threadIdx.x], sh.stats[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// last fallback: binary64 scores of every row for the queries even the FP32
+// rescan could not certify, split into kFbChunks row chunks per query
+
 static_assert(kFbChunks <= 32, "one lane per fallback chunk in the merge");
 
 __global__ void __launch_bounds__(kFbThreads)
 k_fallback_scan(DbView db, CallView call) {
     __shared__ double ws[kFbThreads / 32][FS_MAX_K];
     __shared__ int wi[kFbThreads / 32][FS_MAX_K];
-    const int nfb = *call.fb_count;
+    const int nfb = *call.fb2_count;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
         const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
-        const int q = call.fb_list[slot];
+        const int q = call.fb2_list[slot];
         const SegPlan p = call.plan[plan_of_query(call, q)];
         const int k = p.k;
         const int excl = call.exclude ? call.exclude[q] : -1;
@@ -446,11 +549,11 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
     __shared__ unsigned long long st[2];
     if (threadIdx.x < 2) st[threadIdx.x] = 0;
     __syncthreads();
-    const int nfb = *call.fb_count;
+    const int nfb = *call.fb2_count;
     const int lane = threadIdx.x & 31;
     const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (slot < nfb) {
-        const int q = call.fb_list[slot];
+        const int q = call.fb2_list[slot];
         const SegPlan p = call.plan[plan_of_query(call, q)];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
@@ -556,6 +659,12 @@ cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t s
 
 cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms, cudaStream_t st) {
     if (call.nq == 0) return cudaSuccess;
+    k_fb_scan32<<<num_sms * 2, kFbThreads, 0, st>>>(db, call);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+    k_fb_select<<<num_sms, kSelWarps * 32, 0, st>>>(db, call);
+    e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
     k_fallback_scan<<<num_sms * 2, kFbThreads, 0, st>>>(db, call);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
