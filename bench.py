@@ -208,6 +208,116 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args, fs, torch, dev, world, rank, local):
+    """Serving workload: a device-resident database, requests of 1-1,024
+    queries arriving as a Poisson process, continuous batching with
+    memory-based admission (paper_1810_10496_gb300.serve)."""
+    import torch.distributed as tdist
+    from paper_1810_10496_gb300 import serve
+
+    w = fsgen.make("serving", workers=min(16, _NCPU), n=args.n, q=1)
+    pool = fsgen.query_rows(w.seed + 1, 65536, w.f, workers=min(16, _NCPU))
+    k, slots, max_batch, l_max = w.k[0], args.slots, 1024, 128
+    x_d = torch.from_numpy(w.x).to(dev)
+    off_d = torch.from_numpy(w.seq_off).to(dev)
+    ids_d = torch.from_numpy(w.seq_ids).to(dev)
+
+    def serve_at(prec, rate, duration):
+        db = fs.fs_build_db(x_d, off_d, ids_d, prec=prec)
+        per_batch = (max_batch * w.f * 4 + max_batch * k * (12 + 2 * l_max)
+                     + fs.fs_workspace_size(db, max_batch) + 6 * 256)
+        arena = slots * per_batch
+        eng = serve.GpuEngine(fs, db, w.f, k, slots, max_batch, arena, l_max, dev)
+        srv = serve.Server(eng, arena_bytes=arena, slots=slots, max_batch=max_batch)
+        # warm-up: a few batches of every size class
+        serve.run_open_loop(srv, serve.poisson_requests(pool, rate, min(0.05, duration), 1, 1024, 99))
+        srv.stats = serve.ServerStats()
+        reqs = serve.poisson_requests(pool, rate, duration, 1, 1024, seed=7)
+        # one full batch timed with the stage events: the scan's roofline
+        fs.fs_profile_read(reset=True)
+        fs.fs_profile_enable(True)
+        qd = torch.from_numpy(pool[:max_batch]).to(dev)
+        fs.fs_recommend(db, qd, k)
+        torch.cuda.synchronize()
+        fs.fs_profile_enable(False)
+        prof = fs.fs_profile_read(reset=True)
+        sampler = ClockSampler(local)
+        sampler.__enter__()
+        wall = serve.run_open_loop(srv, reqs)
+        sampler.__exit__(None, None, None)
+        nq = sum(r.queries.shape[0] for r in reqs)
+        res = {"wall_s": wall, "queries": nq, "requests": len(reqs), "batches": srv.stats.batches,
+               "mean_batch": float(np.mean(srv.stats.batch_sizes)),
+               "max_inflight": srv.stats.max_inflight,
+               "admissions_blocked_by_memory": srv.stats.admissions_blocked_by_memory,
+               "arena_bytes": arena, "max_arena_used": srv.stats.max_arena_used,
+               "offered_qps": rate, "served_qps": nq / wall,
+               "clocks": sampler.summary(), "scan_ms_1024": prof["ms"]["scan"]}
+        res.update(serve.latency_summary(reqs))
+        # sample of answers for the oracle check
+        res["_sample"] = reqs[::max(1, len(reqs) // 16)][:16]
+        db.close()
+        del eng, srv
+        return res
+
+    r16 = serve_at(args.precision, args.rate, args.duration)
+    r32 = None
+    if not args.no_fp32_compare:
+        r32 = serve_at("fp32", args.fp32_rate, args.duration)
+    N = w.n
+    value = r16["served_qps"] * N
+    flops = 2.0 * 1024 * N * w.f
+    peaks, peak_src = load_peaks()
+    roof = {"bound": "tensor", "achieved": flops / (r16["scan_ms_1024"] / 1e3) / 1e12,
+            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
+            "kernel": f"scan ({args.precision}), one 1,024-query batch",
+            "peak_source": f"{peak_src} bf16 burst", "kernel_ms": r16["scan_ms_1024"]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": r16["batches"], "warmup": 3, "ms_per_step": r16["wall_s"] * 1e3 / r16["batches"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8_e4m3"}[args.precision] + "+f64 rescoring",
+        "data": "synthetic",
+        "config": {"workload": f"serving: database {N:,} x {w.f} features resident, Poisson "
+                               f"arrivals of requests of 1-1,024 queries, k={k}",
+                   "offered_queries_per_s": args.rate, "duration_s": args.duration,
+                   "slots": slots, "precision": args.precision,
+                   "l2": "inputs larger than L2 (database scanned per batch)"},
+        "queries_per_s": r16["served_qps"], "p50_ms": r16["p50_ms"], "p99_ms": r16["p99_ms"],
+        "clocks": r16["clocks"],
+        "e2e": {"value": value, "unit": UNIT,
+                "h2d_bytes_per_step": int(r16["queries"] * w.f * 4 / r16["batches"]),
+                "d2h_bytes_per_step": int(r16["queries"] * k * (12 + 2 * 128) / r16["batches"]),
+                "note": "the serving loop is end to end: host queries in, host results out"},
+        "gpu_launches": None, "roofline": roof,
+        "serving": {kk: v for kk, v in r16.items() if not kk.startswith("_")},
+        "vs_fp32_scan": None if r32 is None else {
+            "fp32_offered_qps": args.fp32_rate, "fp32_served_qps": r32["served_qps"],
+            "fp32_p50_ms": r32["p50_ms"], "fp32_p99_ms": r32["p99_ms"],
+            "served_qps_ratio": r16["served_qps"] / r32["served_qps"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        exact = True
+        t0 = time.perf_counter()
+        nq = 0
+        for r in r16["_sample"][:4]:
+            i_o, d_o, s_o, l_o = oracle.recommend(w.x, r.queries[:4], k, w.seq_off, w.seq_ids, 128)
+            exact &= bool(np.array_equal(r.idx[:4], i_o) and np.array_equal(r.seqs[:4], s_o))
+            nq += min(4, r.queries.shape[0])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nq * N / dt, "unit": UNIT, "cores": _NCPU,
+                                "kind": "oracle", "sample": f"{nq} served queries against all {N:,} rows",
+                                "seconds": dt, "sample_exact": exact}
+        line["recall"] = 1.0 if exact else None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -225,6 +335,8 @@ def run_ours(args):
     if world > 1:
         tdist.barrier()
     fs.lib()
+    if args.workload == "serving":
+        return run_serving(args, fs, torch, dev, world, rank, local)
 
     t0 = time.perf_counter()
     w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
@@ -446,6 +558,12 @@ def main():
                     help="database rows instead of the workload's (bounded profiling cases)")
     ap.add_argument("--q", type=int, default=None, help="queries instead of the workload's")
     ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--rate", type=float, default=500_000,
+                    help="serving: offered queries per second (Poisson)")
+    ap.add_argument("--fp32-rate", type=float, default=10_000,
+                    help="serving: offered rate for the plain FP32 path")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
+    ap.add_argument("--slots", type=int, default=4, help="serving: batches in flight")
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
