@@ -273,3 +273,78 @@ def test_full_scale_sampled(fs, prec):
     assert st["certified"] + st["fallback"] == w.q
     # every query: the returned rows are ordered and their distances valid
     assert np.all(np.diff(dist, axis=1) >= -1e-6) and np.all((dist >= 0) & (dist <= 1))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_many_uneven_segments(fs, prec):
+    """300 databases of log-uniform size (10..5000 rows), 0-40 queries each,
+    k in {1, 3}: every database's answer equals the oracle's on it alone."""
+    rng = np.random.default_rng(8)
+    sizes = np.floor(np.exp(rng.uniform(np.log(10), np.log(5000), size=300))).astype(np.int64)
+    nq = rng.integers(0, 41, size=300)
+    ks = rng.choice(np.array([1, 3]), size=300)
+    seg = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    qseg = np.concatenate([[0], np.cumsum(nq)]).astype(np.int32)
+    x = fsgen.db_rows(31, int(seg[-1]), 64)
+    qy = fsgen.query_rows(31, int(qseg[-1]), 64)
+    off, ids = fsgen.phase_orders(31, int(seg[-1]))
+    db = build_db(fs, x, off, ids, prec, seg_off=seg)
+    idx, dist, *_ = run(fs, db, qy, ks, q_seg_off=qseg)
+    for s in range(300):
+        a, b = qseg[s], qseg[s + 1]
+        if a == b:
+            continue
+        i_o, d_o, _ = oracle.knn(x[seg[s]:seg[s + 1]], qy[a:b], int(ks[s]))
+        assert_same(idx[a:b], dist[a:b], i_o, d_o)
+
+
+def test_cuda_graph_replay(fs):
+    """A captured call replays to the eager answer, also after the query
+    buffer is refilled (the plan and tensor maps are baked into the graph)."""
+    import torch
+    rng = np.random.default_rng(12)
+    sizes = np.array([3000, 17, 9000, 1200, 0, 4000])
+    nq = np.array([40, 3, 130, 0, 5, 70])
+    ks = np.array([3, 1, 3, 1, 2, 3])
+    seg = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    qseg = np.concatenate([[0], np.cumsum(nq)]).astype(np.int32)
+    x = fsgen.db_rows(41, int(seg[-1]), 128)
+    off, ids = fsgen.phase_orders(41, int(seg[-1]))
+    db = build_db(fs, x, off, ids, "bf16", seg_off=seg)
+    q1 = fsgen.query_rows(41, int(qseg[-1]), 128)
+    q2 = fsgen.query_rows(42, int(qseg[-1]), 128)
+    qd = _dev(q1)
+    ws = torch.empty(fs.fs_workspace_size(db, qd.shape[0], qseg), dtype=torch.uint8, device="cuda")
+    out = dict(idx=torch.empty((qd.shape[0], 3), dtype=torch.int32, device="cuda"),
+               dist=torch.empty((qd.shape[0], 3), dtype=torch.float32, device="cuda"),
+               seq_out=torch.empty((qd.shape[0], 3, 128), dtype=torch.int16, device="cuda"),
+               seq_len=torch.empty((qd.shape[0], 3), dtype=torch.int32, device="cuda"))
+    fs.fs_recommend(db, qd, ks, q_seg_off=qseg, workspace=ws, **out)   # warm-up, eager
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fs.fs_recommend(db, qd, ks, q_seg_off=qseg, workspace=ws, **out)
+    for qh in (q1, q2, q1):
+        qd.copy_(torch.from_numpy(qh))
+        g.replay()
+        torch.cuda.synchronize()
+        gi, gd = out["idx"].cpu().numpy(), out["dist"].cpu().numpy()
+        ei, ed, *_ = run(fs, db, qh, ks, q_seg_off=qseg)
+        assert np.array_equal(gi, ei) and np.array_equal(gd, ed)
+    for s in range(len(sizes)):
+        a, b = qseg[s], qseg[s + 1]
+        if a < b:
+            i_o, d_o, _ = oracle.knn(x[seg[s]:seg[s + 1]], q1[a:b], int(ks[s]))
+            assert_same(gi[a:b], gd[a:b], i_o, d_o)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_mid_size_many_query_tiles(fs, prec):
+    """150,001 rows and 600 queries (5 query tiles, chunked so the chunks in
+    flight fit L2, with a ragged last chunk)."""
+    w = fsgen.make("tiny_k3", n=150_001, q=600, f=128, seed=23)
+    db = build_db(fs, w.x, w.seq_off, w.seq_ids, prec)
+    idx, dist, seqs, lens, _ = run(fs, db, w.queries, 3)
+    i_o, d_o, s_o, l_o = oracle.recommend(w.x, w.queries, 3, w.seq_off, w.seq_ids, 128)
+    assert_same(idx, dist, i_o, d_o)
+    assert np.array_equal(seqs, s_o) and np.array_equal(lens, l_o)
