@@ -272,6 +272,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
+                bool offered = false;   // the list may have changed in this tile
 #pragma unroll 1
                 for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 64) {
                     uint32_t r0[32], r1[32];
@@ -293,12 +294,13 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     float gm[8];
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
-                        const float a = fmaxf(fmaxf(v[8 * g], v[8 * g + 1]), fmaxf(v[8 * g + 2], v[8 * g + 3]));
-                        const float b = fmaxf(fmaxf(v[8 * g + 4], v[8 * g + 5]), fmaxf(v[8 * g + 6], v[8 * g + 7]));
-                        gm[g] = FP8 ? fmaxf(a, b) * sq : fmaxf(a, b);
+                        const float a = fmax3(v[8 * g], v[8 * g + 1], v[8 * g + 2]);
+                        const float b = fmax3(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]);
+                        const float mx = fmax3(a, b, fmaxf(v[8 * g + 6], v[8 * g + 7]));
+                        gm[g] = FP8 ? mx * sq : mx;
                     }
-                    const float m = fmaxf(fmaxf(fmaxf(gm[0], gm[1]), fmaxf(gm[2], gm[3])),
-                                          fmaxf(fmaxf(gm[4], gm[5]), fmaxf(gm[6], gm[7])));
+                    const float m = fmax3(fmax3(gm[0], gm[1], gm[2]), fmax3(gm[3], gm[4], gm[5]),
+                                          fmaxf(gm[6], gm[7]));
                     float thr = fmaxf(st.thr_s, shared_s);
                     if (__any_sync(0xffffffffu, m >= thr)) {
                         // group by group, with the threshold as it stands (a list that
@@ -330,6 +332,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                             st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
                                                      w.p.row0, excl);
                                             thr = fmaxf(st.thr_s, shared_s);
+                                            offered = true;
                                         }
                                     }
                                 }
@@ -340,7 +343,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bars.tmem_empty[acc]));
-                if (qvalid && st.cnt >= w.p.k) {
+                if (qvalid && offered && st.cnt >= w.p.k) {
                     const float kth = st.kth_score(w.p.k);
                     // rounded down: the bound may only err low
                     const float bound = (kth - e2) - fabsf(kth) * 0x1p-20f;
