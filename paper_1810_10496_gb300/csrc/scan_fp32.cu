@@ -76,6 +76,14 @@ k_scan_fp32(DbView db, CallView call) {
 #pragma unroll
         for (int e = 0; e < T; ++e) sm.lists[e][tid] = 0;
         const int excl = (call.exclude && lq < nq_tile) ? call.exclude[qbase + lq] : -1;
+        // the pruning bound shared by every block scanning this query (as in
+        // the tensor-core scan): the k-th best score any list holds minus 2E;
+        // rows below it cannot be among the k nearest
+        const bool qv = lq < nq_tile;
+        uint32_t* shared_p = call.shared_thr + qbase + (qv ? lq : 0);
+        const float e2 =
+            qv ? 2.0f * (p.bound_scan + p.bound_rq * call.q_resid[qbase + lq]) * 1.0001f : 0.0f;
+        float published = -INFINITY;
 
         // global-load mapping: one float4 of A and one of B per thread and step
         const int ld_row = tid >> 1, ld_col = (tid & 1) * 4;
@@ -144,9 +152,12 @@ k_scan_fp32(DbView db, CallView call) {
             // filter: keep this thread's 16 best of its 64 columns
             const float* srow = &sm.s[lq][hf * 64];
             const int64_t col_row0 = tr + hf * 64;
+            // (the initial bound, 0, maps to NaN: fmaxf then keeps thr_s)
+            const float shared_s = qv ? unord_f32(__ldcg(shared_p)) : INFINITY;
+            bool changed = false;
             for (int j = 0; j < 64; ++j) {
                 const float sc = srow[j];
-                if (sc >= thr_s) {
+                if (sc >= fmaxf(thr_s, shared_s)) {
                     const int64_t row = col_row0 + j;
                     const int32_t li = (int32_t)(row - p.row0);
                     if (row < row_end && li != excl) {
@@ -170,7 +181,28 @@ k_scan_fp32(DbView db, CallView call) {
                             thr_key = mn;
                             thr_s = key_score(mn);
                         }
+                        changed = true;
                     }
+                }
+            }
+            if (qv && changed && cnt >= p.k) {
+                // the list's k-th best (keys are distinct), then the bound,
+                // rounded down: it may only err low
+                uint64_t prev = ~0ull, best = 0;
+                for (int r = 0; r < p.k; ++r) {
+                    best = 0;
+#pragma unroll
+                    for (int e = 0; e < T; ++e) {
+                        const uint64_t v = sm.lists[e][tid];
+                        if (v < prev && v > best) best = v;
+                    }
+                    prev = best;
+                }
+                const float kth = key_score(best);
+                const float bound = (kth - e2) - fabsf(kth) * 0x1p-20f;
+                if (bound > published) {
+                    atomicMax(shared_p, ord_f32(bound));
+                    published = bound;
                 }
             }
         }
