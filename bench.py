@@ -44,9 +44,7 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # capture of the current version of that kernel, keyed by (kernel, workload,
 # precision); absent (reported as null) until captured. Source: the matching
 # summary under profiles/.
-TRAFFIC_BYTES = {
-    ("scan_bf16", "fp32_scale", "bf16"): 295.66e6,   # profiles/scan_bf16_fp32_scale.md
-}
+TRAFFIC_BYTES = {}
 
 
 def log(*a):
@@ -246,7 +244,19 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                      + fs.fs_workspace_size(db, max_batch) + 6 * 256)
         arena = slots * per_batch
         eng = serve.GpuEngine(fs, db, w.f, k, slots, max_batch, arena, l_max, dev)
-        srv = serve.Server(eng, arena_bytes=arena, slots=slots, max_batch=max_batch)
+        # a batch of one query tile, timed: the longest a small batch waits
+        # for more queries while another batch is in flight
+        q_tile = torch.from_numpy(pool[:128]).to(dev)
+        fs.fs_recommend(db, q_tile, k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fs.fs_recommend(db, q_tile, k)
+        e1.record()
+        torch.cuda.synchronize()
+        tile_ms = e0.elapsed_time(e1)
+        max_wait = tile_ms / 1e3 if args.max_wait_ms is None else args.max_wait_ms / 1e3
+        srv = serve.Server(eng, arena_bytes=arena, slots=slots, max_batch=max_batch,
+                           min_batch=args.min_batch, max_wait_s=max_wait)
         # warm-up: a few batches of every size class
         serve.run_open_loop(srv, serve.poisson_requests(pool, rate, min(0.05, duration), 1, 1024, 99))
         srv.stats = serve.ServerStats()
@@ -270,7 +280,9 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                "admissions_blocked_by_memory": srv.stats.admissions_blocked_by_memory,
                "arena_bytes": arena, "max_arena_used": srv.stats.max_arena_used,
                "offered_qps": rate, "served_qps": nq / wall,
-               "clocks": sampler.summary(), "scan_ms_1024": prof["ms"]["scan"]}
+               "clocks": sampler.summary(), "scan_ms_1024": prof["ms"]["scan"],
+               "tile_batch_ms": tile_ms, "min_batch": args.min_batch,
+               "max_wait_ms": max_wait * 1e3, "held_for_fill": srv.stats.held_for_fill}
         res.update(serve.latency_summary(reqs))
         # sample of answers for the oracle check
         res["_sample"] = reqs[::max(1, len(reqs) // 16)][:16]
@@ -316,6 +328,7 @@ def run_serving(args, fs, torch, dev, world, rank, local):
         "vs_fp32_scan": None if r32 is None else {
             "fp32_offered_qps": args.fp32_rate, "fp32_served_qps": r32["served_qps"],
             "fp32_p50_ms": r32["p50_ms"], "fp32_p99_ms": r32["p99_ms"],
+            "fp32_mean_batch": r32["mean_batch"], "fp32_tile_batch_ms": r32["tile_batch_ms"],
             "served_qps_ratio": r16["served_qps"] / r32["served_qps"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -345,6 +358,7 @@ def run_ours(args):
 
     import paper_1810_10496_gb300 as fs
     from paper_1810_10496_gb300 import build as libbuild
+    from paper_1810_10496_gb300 import tune as fstune
 
     world, rank, local = setup_dist()
     if world > 1:
@@ -377,8 +391,15 @@ def run_ours(args):
     q_host = torch.from_numpy(w.queries).pin_memory()
     q_d = q_host.to(dev)
 
+    tuned = {}
+
     def make_db(prec):
         db = fs.fs_build_db(x_d, off_d, ids_d, seg_off=seg_off, prec=prec)
+        if not args.no_tune:
+            # the plan parameters for this batch shape, timed before the timed region
+            res = fstune.autotune(db, q_d, ks, q_seg_off=q_seg_off, reps=3, cache_path=None)
+            tuned[prec] = {"tuning": res["tuning"], "ms": res["ms"],
+                           "default_ms": res["default_ms"], "candidates": len(res["tried"])}
         ws = torch.empty(fs.fs_workspace_size(db, Q, q_seg_off), dtype=torch.uint8, device=dev)
         return db, ws
 
@@ -523,6 +544,7 @@ def run_ours(args):
         "config": {"workload": workload_desc(w), "precision": prec,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "cuda_graph": bool(use_graph),
+                   "plan_tuning": tuned if tuned else "defaults (--no-tune)",
                    "l2": f"inputs larger than L2 (database {N * F * (4 if prec == 'fp32' else 2 if prec == 'bf16' else 1) / 1e6:.0f} MB scanned per step)"},
         "queries_per_s": world * Q * args.steps / (total_ms / 1e3),
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
@@ -578,9 +600,15 @@ def main():
                     help="serving: offered rate for the plain FP32 path")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches in flight")
+    ap.add_argument("--min-batch", type=int, default=128,
+                    help="serving: queries a batch waits for while another is in flight")
+    ap.add_argument("--max-wait-ms", type=float, default=None,
+                    help="serving: longest such wait (default: the time of a 128-query batch)")
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default scan plan instead of autotuning it first")
     ap.add_argument("--graph", dest="graph", action="store_true", default=None,
                     help="replay each step as a captured CUDA graph (default: segmented workloads)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")

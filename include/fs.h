@@ -206,6 +206,36 @@ fs_status fs_db_check(fs_db *db, void *stream);
 fs_status fs_db_stats(fs_db *db, void *stream, int32_t reset, fs_stats *out);
 
 /*
+ * Scan planning parameters of one database. The paper has no counterpart:
+ * these only change how the scan's work is split across blocks and how
+ * long its internal candidate lists are, never a result (the selection is
+ * exact whatever they are). A field left 0 takes the built-in default.
+ *   items_per_block  scan work items (query tile x row chunk) per resident
+ *                    block, 1..64; more items balance uneven segments better,
+ *                    fewer keep longer row chunks per item (default 4).
+ *   list_len         entries per candidate list of the tensor-core scans:
+ *                    8 or 16. 8 takes effect only when every k of a call is
+ *                    <= 8 (default: 8 then, else 16). The FP32 scan always
+ *                    keeps 16.
+ *   l2_share_pct     percent of the L2 cache that the row chunks scanned at
+ *                    the same time may fill before they are split further
+ *                    (single-segment databases), 1..100 (default 50);
+ *                    -1 turns the cap off.
+ * fs_workspace_size reflects the tuning set at the time of the call: size
+ * the workspace after fs_db_set_tuning. Neither call may run while calls on
+ * the same database are being issued from another thread. t == NULL restores
+ * the defaults. FS_EINVAL for a field outside its range (nothing changes).
+ */
+typedef struct {
+    int32_t items_per_block;
+    int32_t list_len;
+    int32_t l2_share_pct;
+} fs_tuning;
+
+fs_status fs_db_set_tuning(fs_db *db, const fs_tuning *t);
+fs_status fs_db_get_tuning(const fs_db *db, fs_tuning *out);
+
+/*
  * Stage timing (tracing). While enabled, every fs_knn / fs_recommend call
  * records a CUDA event before and after each of its stages, on the call's
  * stream. fs_profile_read waits for those events and returns, per stage, the

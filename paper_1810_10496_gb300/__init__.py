@@ -46,6 +46,13 @@ class _Profile(ctypes.Structure):
                 ("launches", ctypes.c_uint64)]
 
 
+TUNING_FIELDS = ("items_per_block", "list_len", "l2_share_pct")
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in TUNING_FIELDS]
+
+
 _lib = None
 P = ctypes.c_void_p
 I32, I64, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
@@ -60,6 +67,8 @@ _SIGNATURES = {
     "fs_db_destroy": [P],
     "fs_db_check": [P, P],
     "fs_db_stats": [P, P, I32, ctypes.POINTER(_Stats)],
+    "fs_db_set_tuning": [P, ctypes.POINTER(_Tuning)],
+    "fs_db_get_tuning": [P, ctypes.POINTER(_Tuning)],
     "fs_profile_enable": [I32],
     "fs_profile_read": [I32, ctypes.POINTER(_Profile)],
 }
@@ -282,6 +291,25 @@ def fs_db_stats(db: Database, reset: bool = False, stream=None) -> dict:
     st = _Stats()
     _check(lib().fs_db_stats(db.handle, _stream(stream), 1 if reset else 0, ctypes.byref(st)))
     return {n: int(getattr(st, n)) for n in STAT_FIELDS}
+
+
+def fs_db_set_tuning(db: Database, tuning: dict | None):
+    """Scan planning parameters (``TUNING_FIELDS``; missing or 0 = default;
+    None restores every default). Size workspaces after this call."""
+    if tuning is None:
+        _check(lib().fs_db_set_tuning(db.handle, None))
+        return
+    bad = set(tuning) - set(TUNING_FIELDS)
+    if bad:
+        raise ValueError(f"unknown tuning fields {sorted(bad)}")
+    t = _Tuning(*(int(tuning.get(n, 0)) for n in TUNING_FIELDS))
+    _check(lib().fs_db_set_tuning(db.handle, ctypes.byref(t)))
+
+
+def fs_db_get_tuning(db: Database) -> dict:
+    t = _Tuning()
+    _check(lib().fs_db_get_tuning(db.handle, ctypes.byref(t)))
+    return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
 
 
 def fs_db_destroy(db: Database):

@@ -44,6 +44,7 @@ struct fs_db {
     unsigned long long* stats = nullptr;
     int64_t n_pad = 0;              // rows of the code array (tensor-core scans)
     CUtensorMap map_x;              // TMA map of the codes (tensor-core scans)
+    fs_tuning tune = {0, 0, 0};     // scan planning parameters (0 = default)
 };
 
 namespace {
@@ -252,14 +253,20 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         work += (int64_t)p.qtiles * ceil_div(p.nrows, pl.tile_rows);
     }
     // the tensor-core scan keeps 8-entry lists when every k fits (fewer inserts)
-    pl.list_t = (tensor_scan(db) && !sizing && pl.k_max <= kListTSmall) ? kListTSmall : kListT;
+    const bool small_lists = db->tune.list_len == 0 || db->tune.list_len == kListTSmall;
+    pl.list_t = (tensor_scan(db) && !sizing && small_lists && pl.k_max <= kListTSmall)
+                    ? kListTSmall
+                    : kListT;
     // Row chunking. (1) Items of about work / (4 slots) tiles keep every block
     // busy. (2) Blocks that run at the same time scan about slots / qtiles + 1
     // chunks of a segment; those chunks should fit in half of L2 so the query
     // tiles of a chunk read its rows from L2, not HBM. (3) Among chunk counts
     // meeting (1) and (2), take the one that fills the last round of items
-    // best (blocks take items round robin).
-    const int64_t desired = (int64_t)pl.slots * 4;
+    // best (blocks take items round robin). The 4 and the half are the
+    // defaults of the tuning parameters items_per_block and l2_share_pct.
+    const int items_per_block = db->tune.items_per_block ? db->tune.items_per_block : 4;
+    const int l2_pct = db->tune.l2_share_pct ? db->tune.l2_share_pct : 50;
+    const int64_t desired = (int64_t)pl.slots * items_per_block;
     const int64_t tiles_per_item = std::max<int64_t>(1, ceil_div(work, desired));
     const int64_t row_bytes = tensor_scan(db) ? (int64_t)db->fl * (db->prec == FS_BF16 ? 2 : 1)
                                               : (int64_t)db->fu * 4;
@@ -270,11 +277,12 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         const int64_t row_tiles = ceil_div(p.nrows, pl.tile_rows);
         int64_t chunk_tiles = std::max<int64_t>(1, std::min(row_tiles, tiles_per_item));
         const double live = (double)pl.slots / std::max(1, p.qtiles) + 1.0;
-        if (n_seg == 1 && p.qtiles >= 2 && row_tiles > 1 &&
+        const double l2_share = (double)l2_bytes * l2_pct / 100.0;
+        if (l2_pct > 0 && n_seg == 1 && p.qtiles >= 2 && row_tiles > 1 &&
             live * chunk_tiles * pl.tile_rows * row_bytes > (double)l2_bytes) {
-            // the chunks in flight overflow L2: cap them at half of it
+            // the chunks in flight overflow L2: cap them at a share of it
             const int64_t cap = std::max<int64_t>(
-                1, (int64_t)(l2_bytes / 2 / (live * row_bytes * pl.tile_rows)));
+                1, (int64_t)(l2_share / (live * row_bytes * pl.tile_rows)));
             int64_t c_lo = ceil_div(row_tiles, std::min(chunk_tiles, cap));
             double best = -1.0;
             int64_t best_c = c_lo;
@@ -650,6 +658,28 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
 #undef FS_TRY
 #undef FS_TRY_CUDA
     *out = db;
+    return FS_OK;
+}
+
+fs_status fs_db_set_tuning(fs_db* db, const fs_tuning* t) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    if (!t) {
+        db->tune = fs_tuning{0, 0, 0};
+        return FS_OK;
+    }
+    if (t->items_per_block < 0 || t->items_per_block > 64)
+        return fail(FS_EINVAL, "items_per_block=%d is outside 0..64", t->items_per_block);
+    if (t->list_len != 0 && t->list_len != kListTSmall && t->list_len != kListT)
+        return fail(FS_EINVAL, "list_len=%d is not 0, %d or %d", t->list_len, kListTSmall, kListT);
+    if (t->l2_share_pct < -1 || t->l2_share_pct > 100)
+        return fail(FS_EINVAL, "l2_share_pct=%d is outside -1..100", t->l2_share_pct);
+    db->tune = *t;
+    return FS_OK;
+}
+
+fs_status fs_db_get_tuning(const fs_db* db, fs_tuning* out) {
+    if (!db || !out) return fail(FS_EINVAL, "db and out must be non-NULL");
+    *out = db->tune;
     return FS_OK;
 }
 

@@ -1,0 +1,51 @@
+"""Autotuner host logic on the CPU: candidate sets, cache keys and file,
+and the choice (fastest wins, a candidate with other answers is an error)."""
+import json
+
+import pytest
+
+from paper_1810_10496_gb300 import tune
+
+
+def test_candidates_shape_rules():
+    bf = tune.candidates("bf16", 1, 3)
+    assert bf[0] == {"items_per_block": 0, "list_len": 0, "l2_share_pct": 0}
+    # every distinct (items, list, share) once, the default not repeated
+    norm = [tune._normal(c) for c in bf]
+    assert len(norm) == len(set(norm))
+    assert len(bf) == len(tune.ITEMS_PER_BLOCK) * len(tune.LIST_LEN) * len(tune.L2_SHARE_PCT)
+    # several segments: no L2 share; k > 8 or FP32: no list length
+    multi = tune.candidates("bf16", 512, 3)
+    assert {c["l2_share_pct"] for c in multi} == {0}
+    assert {c["list_len"] for c in tune.candidates("bf16", 1, 16)} == {0}
+    assert {c["list_len"] for c in tune.candidates("fp32", 1, 3)} == {0}
+
+
+def test_shape_key_buckets():
+    a = tune.shape_key("GB300", "bf16", 128, 1_000_000, 4000, 1, 3)
+    b = tune.shape_key("GB300", "bf16", 128, 1_048_576, 4096, 1, 3)
+    assert a == b and "N1048576" in a and "Q4096" in a
+    assert a != tune.shape_key("GB300", "bf16", 128, 1_048_577, 4096, 1, 3)
+    assert a != tune.shape_key("GB300", "fp8", 128, 1_048_576, 4096, 1, 3)
+    assert tune.shape_key("x", "bf16", 8, 0, 0, 1, 1).startswith("x|bf16|F8|N0|Q0|S1")
+
+
+def test_cache_round_trip(tmp_path):
+    p = str(tmp_path / "sub" / "t.json")
+    assert tune.load_cache(p) == {}
+    tune.save_cache({"k": {"tuning": {"items_per_block": 8}, "ms": 1.0}}, p)
+    assert tune.load_cache(p)["k"]["ms"] == 1.0
+    (tmp_path / "bad.json").write_text("{not json")
+    assert tune.load_cache(str(tmp_path / "bad.json")) == {}
+    assert json.load(open(p))["k"]["tuning"]["items_per_block"] == 8
+
+
+def test_choose_fastest_and_consistency():
+    cands = tune.candidates("bf16", 1, 3)
+    times = {tune._normal(c): 10.0 - i * 0.1 for i, c in enumerate(cands)}
+    times[tune._normal(cands[5])] = 0.5
+    res = tune.choose(lambda c: (times[tune._normal(c)], "same"), cands, lambda a, b: a == b)
+    assert res["tuning"] == cands[5] and res["ms"] == 0.5
+    assert res["default_ms"] == 10.0 and len(res["tried"]) == len(cands)
+    with pytest.raises(RuntimeError):
+        tune.choose(lambda c: (1.0, tune._normal(c)), cands, lambda a, b: a == b)
