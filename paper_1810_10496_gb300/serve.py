@@ -100,19 +100,30 @@ class ServerStats:
     max_inflight: int = 0
     max_arena_used: int = 0
     admissions_blocked_by_memory: int = 0
+    held_for_fill: int = 0
     batch_sizes: list = field(default_factory=list)
 
 
 class Server:
     """Continuous batching over `engine` with at most `slots` batches in
     flight, at most `max_batch` queries per batch and `arena_bytes` of
-    transient device memory."""
+    transient device memory.
 
-    def __init__(self, engine, arena_bytes: int, slots: int = 4, max_batch: int = 1024):
+    While another batch is in flight, a new one waits until it holds
+    `min_batch` queries or its oldest request has waited `max_wait_s`: the
+    scan's cost is flat up to one query tile (128 queries), so a batch of a
+    few queries launched next to a running one costs nearly as much as a
+    full tile. With nothing in flight a batch starts at once."""
+
+    def __init__(self, engine, arena_bytes: int, slots: int = 4, max_batch: int = 1024,
+                 min_batch: int = 1, max_wait_s: float = 0.0):
         self.engine = engine
         self.arena = Arena(arena_bytes)
         self.slots = slots
         self.max_batch = max_batch
+        self.min_batch = min_batch
+        self.max_wait_s = max_wait_s
+        self.queued = 0                        # queries waiting
         self.queue = collections.deque()
         self.inflight: list[_Batch] = []
         self.free_slots = list(range(slots))
@@ -124,6 +135,7 @@ class Server:
         if self.engine.batch_bytes(req.queries.shape[0]) > self.arena.size:
             raise ValueError("a request needs more device memory than the whole arena")
         self.queue.append(req)
+        self.queued += req.queries.shape[0]
 
     def _complete(self, now_fn):
         still = []
@@ -143,8 +155,12 @@ class Server:
                 still.append(b)
         self.inflight = still
 
-    def _admit(self):
+    def _admit(self, now: float):
         while self.queue and self.free_slots:
+            if (self.inflight and self.queued < self.min_batch
+                    and now - self.queue[0].arrival < self.max_wait_s):
+                self.stats.held_for_fill += 1
+                return
             # the longest prefix of the queue that fits one batch and the arena
             take, nq = [], 0
             for r in self.queue:
@@ -161,6 +177,7 @@ class Server:
             mem = self.arena.alloc(self.engine.batch_bytes(nq))
             for _ in take:
                 self.queue.popleft()
+            self.queued -= nq
             slot = self.free_slots.pop()
             q = np.concatenate([r.queries for r in take]) if len(take) > 1 else take[0].queries
             handle = self.engine.launch(q, mem[0], slot)
@@ -175,7 +192,7 @@ class Server:
     def poll(self, now_fn=time.perf_counter):
         """Retire finished batches, then admit queued requests."""
         self._complete(now_fn)
-        self._admit()
+        self._admit(now_fn())
 
     def idle(self) -> bool:
         return not self.queue and not self.inflight

@@ -120,3 +120,34 @@ def test_poisson_arrivals_rate():
     nq = sum(r.queries.shape[0] for r in reqs)
     assert abs(nq / 2.0 - 100_000) / 100_000 < 0.05
     assert all(np.diff([r.arrival for r in reqs]) >= 0)
+
+
+def test_min_fill_holds_small_batches_only_while_busy():
+    """With a batch in flight, a small new batch waits for min_batch queries
+    or max_wait_s; with nothing in flight it starts at once; every request
+    is still answered."""
+    clock = FakeClock()
+    eng = FakeEngine(clock, latency=0.005)
+    srv = serve.Server(eng, arena_bytes=400_000, slots=4, max_batch=128, min_batch=64,
+                       max_wait_s=0.003)
+    rng = np.random.default_rng(5)
+    reqs = [serve.Request(i, 0.0004 * i, rng.integers(0, 9, size=(4, 8)).astype(np.float32))
+            for i in range(200)]
+    serve.run_open_loop(srv, reqs, clock=clock, max_wall_s=1e6)
+    assert all(r.done is not None for r in reqs)
+    st = srv.stats
+    assert st.held_for_fill > 0
+    # the first batch went alone at once: nothing was in flight
+    assert eng.launched[0][1] == 4
+    # later batches either filled up or waited out max_wait_s: far fewer
+    # launches than with the greedy policy
+    greedy_clock = FakeClock()
+    greedy_eng = FakeEngine(greedy_clock, latency=0.005)
+    greedy = serve.Server(greedy_eng, arena_bytes=400_000, slots=4, max_batch=128)
+    reqs2 = [serve.Request(r.rid, r.arrival, r.queries) for r in reqs]
+    serve.run_open_loop(greedy, reqs2, clock=greedy_clock, max_wall_s=1e6)
+    assert st.batches < greedy.stats.batches
+    # no request waited in the queue much beyond max_wait_s plus one batch
+    assert max(r.latency for r in reqs) < 0.003 + 3 * 0.005 + 0.01
+    for r in reqs:
+        assert np.array_equal(r.idx, (r.queries[:, :3] * 10).astype(np.int32))
