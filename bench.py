@@ -401,7 +401,10 @@ def run_ours(args):
 
     def make_db(prec):
         db = fs.fs_build_db(x_d, off_d, ids_d, seg_off=seg_off, prec=prec)
-        if tune_plan:
+        if args.tuning:
+            fs.fs_db_set_tuning(db, json.loads(args.tuning))
+            tuned[prec] = {"tuning": fs.fs_db_get_tuning(db), "fixed": True}
+        elif tune_plan:
             # the plan parameters for this batch shape, timed before the timed region
             res = fstune.autotune(db, q_d, ks, q_seg_off=q_seg_off, reps=3, cache_path=None)
             tuned[prec] = {"tuning": res["tuning"], "ms": res["ms"],
@@ -618,6 +621,8 @@ def main():
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,
                     help="autotune the scan plan before timing (default: segmented workloads)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--tuning", default=None,
+                    help='a fixed scan plan tuning instead, e.g. \'{"list_len": 4}\'')
     ap.add_argument("--graph", dest="graph", action="store_true", default=None,
                     help="replay each step as a captured CUDA graph (default: segmented workloads)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")

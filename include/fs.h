@@ -214,9 +214,13 @@ fs_status fs_db_stats(fs_db *db, void *stream, int32_t reset, fs_stats *out);
  *                    block, 1..64; more items balance uneven segments better,
  *                    fewer keep longer row chunks per item (default 4).
  *   list_len         entries per candidate list of the tensor-core scans:
- *                    8 or 16. 8 takes effect only when every k of a call is
- *                    <= 8 (default: 8 then, else 16). The FP32 scan always
- *                    keeps 16.
+ *                    4, 8 or 16. 4 takes effect only when every k of a call
+ *                    is <= 4, 8 only when every k is <= 8; otherwise the
+ *                    next longer list is kept (default: 8 when every k <= 8,
+ *                    else 16). Shorter lists mean fewer inserts, but a list
+ *                    that holds fewer rows than lie within the score error
+ *                    of the k-th best sends its query to the exact fallback.
+ *                    The FP32 scan always keeps 16.
  *   l2_share_pct     percent of the L2 cache that the row chunks scanned at
  *                    the same time may fill before they are split further
  *                    (single-segment databases), 1..100 (default 50);

@@ -252,11 +252,16 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.lists = lists;
         work += (int64_t)p.qtiles * ceil_div(p.nrows, pl.tile_rows);
     }
-    // the tensor-core scan keeps 8-entry lists when every k fits (fewer inserts)
-    const bool small_lists = db->tune.list_len == 0 || db->tune.list_len == kListTSmall;
-    pl.list_t = (tensor_scan(db) && !sizing && small_lists && pl.k_max <= kListTSmall)
-                    ? kListTSmall
-                    : kListT;
+    // the tensor-core scan keeps 8-entry lists when every k fits (fewer
+    // inserts), or 4-entry ones when tuned so and every k <= 4
+    pl.list_t = kListT;
+    if (tensor_scan(db) && !sizing) {
+        const int want = db->tune.list_len ? db->tune.list_len : kListTSmall;
+        if (want == kListTTiny && pl.k_max <= kListTTiny)
+            pl.list_t = kListTTiny;
+        else if (want <= kListTSmall && pl.k_max <= kListTSmall)
+            pl.list_t = kListTSmall;
+    }
     // Row chunking. (1) Items of about work / (4 slots) tiles keep every block
     // busy. (2) Blocks that run at the same time scan about slots / qtiles + 1
     // chunks of a segment; those chunks should fit in half of L2 so the query
@@ -669,8 +674,10 @@ fs_status fs_db_set_tuning(fs_db* db, const fs_tuning* t) {
     }
     if (t->items_per_block < 0 || t->items_per_block > 64)
         return fail(FS_EINVAL, "items_per_block=%d is outside 0..64", t->items_per_block);
-    if (t->list_len != 0 && t->list_len != kListTSmall && t->list_len != kListT)
-        return fail(FS_EINVAL, "list_len=%d is not 0, %d or %d", t->list_len, kListTSmall, kListT);
+    if (t->list_len != 0 && t->list_len != kListTTiny && t->list_len != kListTSmall &&
+        t->list_len != kListT)
+        return fail(FS_EINVAL, "list_len=%d is not 0, %d, %d or %d", t->list_len, kListTTiny,
+                    kListTSmall, kListT);
     if (t->l2_share_pct < -1 || t->l2_share_pct > 100)
         return fail(FS_EINVAL, "l2_share_pct=%d is outside -1..100", t->l2_share_pct);
     db->tune = *t;

@@ -19,6 +19,7 @@ namespace fsk {
 constexpr int kWarp = 32;
 constexpr int kListT = 16;        // largest candidate list (>= FS_MAX_K)
 constexpr int kListTSmall = 8;    // list size when every k <= 8
+constexpr int kListTTiny = 4;     // list size when every k <= 4 (a tuning choice)
 constexpr int kWindow = 64;       // candidates the rerank takes per query
 constexpr int kQTile = 128;       // queries per scan work item
 constexpr int kFbChunks = 32;     // row chunks per query in the exact fallback
@@ -59,15 +60,16 @@ __device__ __forceinline__ int32_t key_index(uint64_t key) {
     return (int32_t)(0xffffffffu - (uint32_t)key);
 }
 
-// One thread's candidate list, held in registers: LT keys (every index is a
-// compile-time constant, so the array never leaves the register file).
+// One thread's candidate list, held in registers: its LT best keys in
+// descending order, zeros while filling (every index is a compile-time
+// constant, so the array never leaves the register file). A key is inserted
+// by one compare-and-exchange pass; the lowest kept key is always the last.
 template <int LT>
 struct RegList {
     uint64_t k[LT];
     uint64_t thr_key;  // lowest key kept once the list is full (0 before)
     float thr_s;       // its score; -inf while the list is filling
-    int cnt;           // keys stored so far
-    int min_slot;      // slot of thr_key
+    int cnt;           // keys stored so far (at most LT)
 
     __device__ __forceinline__ void reset() {
 #pragma unroll
@@ -75,44 +77,18 @@ struct RegList {
         thr_key = 0;
         thr_s = -INFINITY;
         cnt = 0;
-        min_slot = 0;
     }
 
-    // new minimum: a tree over the slots
-    __device__ __forceinline__ void recompute() {
-        uint64_t m[LT];
-        int slot[LT];
+    // Score of the kk-th best key held (1 <= kk <= cnt): the least of the
+    // first kk, taken as a minimum so that no index is computed at run time.
+    __device__ __forceinline__ float kth_score(int kk) const {
+        uint64_t t = ~0ull;
 #pragma unroll
         for (int e = 0; e < LT; ++e) {
-            m[e] = k[e];
-            slot[e] = e;
+            const uint64_t c = e < kk ? k[e] : ~0ull;
+            t = c < t ? c : t;
         }
-#pragma unroll
-        for (int w = LT / 2; w > 0; w >>= 1) {
-#pragma unroll
-            for (int e = 0; e < w; ++e) {
-                const bool lo = m[e + w] < m[e];
-                m[e] = lo ? m[e + w] : m[e];
-                slot[e] = lo ? slot[e + w] : slot[e];
-            }
-        }
-        thr_key = m[0];
-        min_slot = slot[0];
-        thr_s = key_score(m[0]);
-    }
-
-    // Score of the kk-th best key held (kk <= cnt): kk rounds of a maximum
-    // below the previous one (keys are distinct: each holds its row).
-    __device__ __forceinline__ float kth_score(int kk) const {
-        uint64_t prev = ~0ull, best = 0;
-        for (int r = 0; r < kk; ++r) {
-            best = 0;
-#pragma unroll
-            for (int e = 0; e < LT; ++e)
-                if (k[e] < prev && k[e] > best) best = k[e];
-            prev = best;
-        }
-        return key_score(best);
+        return key_score(t);
     }
 
     // Offers (score, row): kept if the list is filling or it beats the lowest.
@@ -120,19 +96,20 @@ struct RegList {
                                           int excl) {
         const int32_t li = (int32_t)(row - row0);
         if (row >= row_end || li == excl) return;
-        const uint64_t key = make_key(v, (uint32_t)li);
-        int at;
-        if (cnt < LT) {
-            at = cnt++;
-        } else if (key > thr_key) {
-            at = min_slot;
-        } else {
-            return;
-        }
+        uint64_t x = make_key(v, (uint32_t)li);
+        if (x <= thr_key) return;
 #pragma unroll
-        for (int e = 0; e < LT; ++e)
-            if (e == at) k[e] = key;
-        if (cnt == LT) recompute();
+        for (int e = 0; e < LT; ++e) {
+            const uint64_t a = k[e];
+            const bool up = x > a;
+            k[e] = up ? x : a;
+            x = up ? a : x;
+        }
+        cnt += cnt < LT ? 1 : 0;
+        if (k[LT - 1] != 0) {
+            thr_key = k[LT - 1];
+            thr_s = key_score(thr_key);
+        }
     }
 };
 #endif

@@ -445,6 +445,9 @@ cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtenso
     const bool fp8 = db.prec == FS_FP8_E4M3;
     const int kblocks = (int)(db.fl * (fp8 ? 1 : 2) / 128);
     if (kblocks < 1 || kblocks > kMaxKBlocks) return cudaErrorInvalidValue;
+    if (list_t == kListTTiny)
+        return fp8 ? launch_variant<true, kListTTiny>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListTTiny>(db, call, map_q, map_x, grid, kblocks, st);
     if (list_t == kListTSmall)
         return fp8 ? launch_variant<true, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st)
                    : launch_variant<false, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st);

@@ -24,7 +24,7 @@ DEFAULT_CACHE = os.environ.get(
     os.path.join(os.path.expanduser("~"), ".cache", "paper_1810_10496_gb300", "tuning.json"))
 
 ITEMS_PER_BLOCK = (2, 4, 8, 16)
-LIST_LEN = (8, 16)
+LIST_LEN = (4, 8, 16)
 L2_SHARE_PCT = (25, 50, -1)
 
 
@@ -32,21 +32,34 @@ def candidates(prec: str, n_seg: int, k_max: int) -> list[dict]:
     """The tunings worth timing for this shape: the list length matters only
     for the tensor-core scans with every k <= 8, the L2 share only for a
     single segment. The defaults come first."""
-    lists = LIST_LEN if (prec != "fp32" and k_max <= 8) else (0,)
+    lists = tuple(n for n in LIST_LEN if n >= k_max and n < 16) if prec != "fp32" else ()
+    lists = lists or (0,)
     shares = L2_SHARE_PCT if n_seg == 1 else (0,)
     out = [{"items_per_block": 0, "list_len": 0, "l2_share_pct": 0}]
+    seen = {_normal(out[0], prec, k_max)}
     for i in ITEMS_PER_BLOCK:
         for ln in lists:
             for p in shares:
                 c = {"items_per_block": i, "list_len": ln, "l2_share_pct": p}
-                if _normal(c) != _normal(out[0]):
+                if _normal(c, prec, k_max) not in seen:
+                    seen.add(_normal(c, prec, k_max))
                     out.append(c)
     return out
 
 
-def _normal(c: dict) -> tuple:
-    """A tuning with the defaults written out (to drop duplicates)."""
-    return (c.get("items_per_block") or 4, c.get("list_len") or 8, c.get("l2_share_pct") or 50)
+def _normal(c: dict, prec: str = "bf16", k_max: int = 1) -> tuple:
+    """A tuning with the defaults written out and the list length the
+    library will actually keep (to drop duplicates)."""
+    want = c.get("list_len") or 8
+    if prec == "fp32":
+        ln = 16
+    elif want == 4 and k_max <= 4:
+        ln = 4
+    elif want <= 8 and k_max <= 8:
+        ln = 8
+    else:
+        ln = 16
+    return (c.get("items_per_block") or 4, ln, c.get("l2_share_pct") or 50)
 
 
 def _bucket(v: int) -> int:

@@ -153,6 +153,25 @@ def test_ties_and_duplicates_take_lower_index(fs, prec):
     assert st["fallback"] >= 1 and st["certified"] + st["fallback"] == 6
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_four_entry_lists(fs, prec):
+    """The 4-entry candidate lists of the tensor-core scans (a tuning): k = 3
+    and k = 4 on random rows, and k = 3 with 20 copies of a query's best row
+    (more rows tied than a list holds, so the fallback answers)."""
+    w = fsgen.make("tiny_k3", n=20_000, q=200, f=64, seed=17)
+    x = w.x.copy()
+    x[5000:5020] = x[11]
+    qy = w.queries.copy()
+    qy[0] = x[11]
+    db = build_db(fs, x, w.seq_off, w.seq_ids, prec)
+    fs.fs_db_set_tuning(db, {"list_len": 4})
+    for k in (3, 4):
+        idx, dist, *_ = run(fs, db, qy, k)
+        i_o, d_o, _ = oracle.knn(x, qy, k)
+        assert_same(idx, dist, i_o, d_o)
+    assert list(idx[0, :3]) == [11, 5000, 5001]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_leave_one_out(fs, prec):
     """Sec. 4.2: each kernel queries the database without its own entry."""

@@ -11,9 +11,13 @@ def test_candidates_shape_rules():
     bf = tune.candidates("bf16", 1, 3)
     assert bf[0] == {"items_per_block": 0, "list_len": 0, "l2_share_pct": 0}
     # every distinct (items, list, share) once, the default not repeated
-    norm = [tune._normal(c) for c in bf]
+    norm = [tune._normal(c, "bf16", 3) for c in bf]
     assert len(norm) == len(set(norm))
-    assert len(bf) == len(tune.ITEMS_PER_BLOCK) * len(tune.LIST_LEN) * len(tune.L2_SHARE_PCT)
+    # list lengths 4 and 8 (16 is never better when every k fits in 8)
+    assert len(bf) == len(tune.ITEMS_PER_BLOCK) * 2 * len(tune.L2_SHARE_PCT)
+    assert {c["list_len"] for c in bf} == {0, 4, 8}
+    # k = 5: lists of 4 cannot hold the answer
+    assert {c["list_len"] for c in tune.candidates("bf16", 1, 5)} == {0, 8}
     # several segments: no L2 share; k > 8 or FP32: no list length
     multi = tune.candidates("bf16", 512, 3)
     assert {c["l2_share_pct"] for c in multi} == {0}
@@ -42,10 +46,11 @@ def test_cache_round_trip(tmp_path):
 
 def test_choose_fastest_and_consistency():
     cands = tune.candidates("bf16", 1, 3)
-    times = {tune._normal(c): 10.0 - i * 0.1 for i, c in enumerate(cands)}
-    times[tune._normal(cands[5])] = 0.5
-    res = tune.choose(lambda c: (times[tune._normal(c)], "same"), cands, lambda a, b: a == b)
+    times = {tune._normal(c, "bf16", 3): 10.0 - i * 0.1 for i, c in enumerate(cands)}
+    times[tune._normal(cands[5], "bf16", 3)] = 0.5
+    res = tune.choose(lambda c: (times[tune._normal(c, "bf16", 3)], "same"), cands,
+                      lambda a, b: a == b)
     assert res["tuning"] == cands[5] and res["ms"] == 0.5
     assert res["default_ms"] == 10.0 and len(res["tried"]) == len(cands)
     with pytest.raises(RuntimeError):
-        tune.choose(lambda c: (1.0, tune._normal(c)), cands, lambda a, b: a == b)
+        tune.choose(lambda c: (1.0, tune._normal(c, "bf16", 3)), cands, lambda a, b: a == b)
