@@ -225,6 +225,10 @@ fs_status fs_db_stats(fs_db *db, void *stream, int32_t reset, fs_stats *out);
  *                    the same time may fill before they are split further
  *                    (single-segment databases), 1..100 (default 50);
  *                    -1 turns the cap off.
+ *   scan_pairs       1: the tensor-core scans run on clusters of two SMs
+ *                    (cta_group::2 MMAs of 256 queries x 256 rows, each SM
+ *                    loading half of the rows); -1 or 0 (default): one SM per
+ *                    tile. Ignored by the FP32 scan.
  * fs_workspace_size reflects the tuning set at the time of the call: size
  * the workspace after fs_db_set_tuning. Neither call may run while calls on
  * the same database are being issued from another thread. t == NULL restores
@@ -234,6 +238,7 @@ typedef struct {
     int32_t items_per_block;
     int32_t list_len;
     int32_t l2_share_pct;
+    int32_t scan_pairs;
 } fs_tuning;
 
 fs_status fs_db_set_tuning(fs_db *db, const fs_tuning *t);

@@ -46,7 +46,7 @@ class _Profile(ctypes.Structure):
                 ("launches", ctypes.c_uint64)]
 
 
-TUNING_FIELDS = ("items_per_block", "list_len", "l2_share_pct")
+TUNING_FIELDS = ("items_per_block", "list_len", "l2_share_pct", "scan_pairs")
 
 
 class _Tuning(ctypes.Structure):

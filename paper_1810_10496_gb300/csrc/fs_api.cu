@@ -44,7 +44,8 @@ struct fs_db {
     unsigned long long* stats = nullptr;
     int64_t n_pad = 0;              // rows of the code array (tensor-core scans)
     CUtensorMap map_x;              // TMA map of the codes (tensor-core scans)
-    fs_tuning tune = {0, 0, 0};     // scan planning parameters (0 = default)
+    CUtensorMap map_x_half;         // the same with half-tile boxes (pairs of CTAs)
+    fs_tuning tune = {0, 0, 0, 0};  // scan planning parameters (0 = default)
 };
 
 namespace {
@@ -202,7 +203,8 @@ struct Plan {
     int64_t total_cand = 0;
     int k_max = 0;
     int tile_rows = 0;
-    int slots = 0;
+    int slots = 0;                  // resident scan blocks, or pairs of blocks
+    bool pair = false;              // tensor-core scan on pairs of SMs
     int list_t = kListT;
 };
 
@@ -233,6 +235,14 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
     pl.tile_rows = tensor_scan(db) ? kTcTileRows : kFp32TileRows;
     const int lists = tensor_scan(db) ? kTcLists : kFp32Lists;
     pl.slots = std::max(1, scan_slots(db));
+    if (tensor_scan(db) && db->tune.scan_pairs > 0) {
+        const int kblocks = (int)(db->fl * (db->prec == FS_BF16 ? 2 : 1) / 128);
+        const int pairs = scan_tc_pair_slots(db->prec == FS_FP8_E4M3, kblocks);
+        if (pairs > 0) {
+            pl.pair = true;
+            pl.slots = pairs;
+        }
+    }
     pl.seg.resize(n_seg);
     pl.k_max = 0;
     int64_t work = 0;  // (query tile, row tile) pairs
@@ -249,8 +259,9 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.nq = q_seg_off ? q_seg_off[s + 1] - q_seg_off[s] : nq;
         p.k = ks;
         p.qtiles = (int)ceil_div(p.nq, kQTile);
+        p.units = pl.pair ? (int)ceil_div(p.qtiles, 2) : p.qtiles;
         p.lists = lists;
-        work += (int64_t)p.qtiles * ceil_div(p.nrows, pl.tile_rows);
+        work += (int64_t)p.units * ceil_div(p.nrows, pl.tile_rows);
     }
     // the tensor-core scan keeps 8-entry lists when every k fits (fewer
     // inserts), or 4-entry ones when tuned so and every k <= 4
@@ -281,9 +292,9 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         SegPlan& p = pl.seg[s];
         const int64_t row_tiles = ceil_div(p.nrows, pl.tile_rows);
         int64_t chunk_tiles = std::max<int64_t>(1, std::min(row_tiles, tiles_per_item));
-        const double live = (double)pl.slots / std::max(1, p.qtiles) + 1.0;
+        const double live = (double)pl.slots / std::max(1, p.units) + 1.0;
         const double l2_share = (double)l2_bytes * l2_pct / 100.0;
-        if (l2_pct > 0 && n_seg == 1 && p.qtiles >= 2 && row_tiles > 1 &&
+        if (l2_pct > 0 && n_seg == 1 && p.units >= 2 && row_tiles > 1 &&
             live * chunk_tiles * pl.tile_rows * row_bytes > (double)l2_bytes) {
             // the chunks in flight overflow L2: cap them at a share of it
             const int64_t cap = std::max<int64_t>(
@@ -292,7 +303,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
             double best = -1.0;
             int64_t best_c = c_lo;
             for (int64_t c = c_lo; c <= std::min(row_tiles, c_lo + 64); ++c) {
-                const int64_t items = c * p.qtiles;
+                const int64_t items = c * p.units;
                 const double fill = (double)items / (double)(ceil_div(items, pl.slots) * pl.slots);
                 if (fill > best + 1e-3) {
                     best = fill;
@@ -309,7 +320,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.bound_scan = (float)b.scan;
         p.bound_rq = (float)b.rq;
         p.bound_rerank = (float)b.rerank;
-        if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.qtiles * row_tiles;
+        if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.units * row_tiles;
     }
     // number the scan items largest segment first: blocks take items round
     // robin, so the long ones start first and the short ones fill in
@@ -325,7 +336,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.item0 = item;
         p.cand0 = cand;
         if (p.nq > 0 && p.nrows > 0) {
-            item += (int64_t)p.qtiles * p.chunks;
+            item += (int64_t)p.units * p.chunks;
             cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
         }
         sorted[i] = p;
@@ -466,13 +477,15 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     }
     if (pl.total_items > 0) {
         StageTimer t(FS_STAGE_SCAN, cs);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.total_items, pl.slots));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.total_items, pl.slots)) *
+                         (pl.pair ? 2 : 1);
         if (tensor_scan(db)) {
             CUtensorMap map_q;
             const int eb = db->prec == FS_BF16 ? 2 : 1;
             FS_CUDA(make_code_map(&map_q, c.q_lowp, round_up(nq, kTcQueryRows), db->fl, eb,
                                   kTcQueryRows));
-            FS_CUDA(launch_scan_tc(v, c, map_q, db->map_x, grid, pl.list_t, cs));
+            FS_CUDA(launch_scan_tc(v, c, map_q, pl.pair ? db->map_x_half : db->map_x, grid,
+                                   pl.list_t, pl.pair, cs));
         } else {
             FS_CUDA(launch_scan_fp32(v, c, grid, cs));
         }
@@ -630,6 +643,8 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
         FS_TRY(alloc(&db->lowp, eb * (size_t)db->n_pad * db->fl, "codes"));
         FS_TRY_CUDA(cudaMemsetAsync(db->lowp, 0, eb * (size_t)db->n_pad * db->fl, cs));
         FS_TRY_CUDA(make_code_map(&db->map_x, db->lowp, db->n_pad, db->fl, eb, kTcTileRows));
+        FS_TRY_CUDA(
+            make_code_map(&db->map_x_half, db->lowp, db->n_pad, db->fl, eb, kTcTileRows / 2));
     }
     if (prec == FS_FP8_E4M3) FS_TRY(alloc((void**)&db->scale, sizeof(float) * n, "scales"));
     if (n > 0) {
@@ -669,7 +684,7 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
 fs_status fs_db_set_tuning(fs_db* db, const fs_tuning* t) {
     if (!db) return fail(FS_EINVAL, "db is NULL");
     if (!t) {
-        db->tune = fs_tuning{0, 0, 0};
+        db->tune = fs_tuning{0, 0, 0, 0};
         return FS_OK;
     }
     if (t->items_per_block < 0 || t->items_per_block > 64)
@@ -680,6 +695,8 @@ fs_status fs_db_set_tuning(fs_db* db, const fs_tuning* t) {
                     kListTSmall, kListT);
     if (t->l2_share_pct < -1 || t->l2_share_pct > 100)
         return fail(FS_EINVAL, "l2_share_pct=%d is outside -1..100", t->l2_share_pct);
+    if (t->scan_pairs < -1 || t->scan_pairs > 1)
+        return fail(FS_EINVAL, "scan_pairs=%d is outside -1..1", t->scan_pairs);
     db->tune = *t;
     return FS_OK;
 }

@@ -132,7 +132,7 @@ struct SegPlan {
     float bound_scan;    // |approximate score - exact cosine| <= bound_scan
     float bound_rq;      //   + bound_rq * (query residual norm), per query
     float bound_rerank;  // same bound for the FP32 rescoring of the window
-    int32_t pad_;
+    int32_t units;       // scan units per row chunk: query tiles, or pairs of them
 };
 static_assert(sizeof(SegPlan) == 80, "SegPlan layout");
 
@@ -223,11 +223,15 @@ int scan_fp32_ctas_per_sm();
 constexpr int kTcTileRows = 256;
 constexpr int kTcQueryRows = 128;
 constexpr int kTcLists = 2;        // candidate lists per (query, chunk): tile halves
-size_t scan_tc_smem_bytes(int kblocks, int stages);
-int scan_tc_stages(int kblocks, bool fp8);
+size_t scan_tc_smem_bytes(int kblocks, int stages, bool pair);
+int scan_tc_stages(int kblocks, bool fp8, bool pair);
+int scan_tc_pair_slots(bool fp8, int kblocks);
 cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int cols,
                           int elem_bytes, int box_rows);
+// pair: clusters of two CTAs (cta_group::2); grid is then even and map_x's
+// box is half a tile (kTcTileRows / 2 rows)
 cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
-                           const CUtensorMap& map_x, int grid, int list_t, cudaStream_t st);
+                           const CUtensorMap& map_x, int grid, int list_t, bool pair,
+                           cudaStream_t st);
 
 }  // namespace fsk

@@ -64,6 +64,8 @@ struct Bars {
     uint64_t a_empty;
     uint64_t drain;
     uint64_t sx_ready[kAccs];   // FP8: the tile's row scales are staged
+    uint64_t pfull[kMaxStages]; // pairs (leader): the odd CTA's ring slot landed
+    uint64_t pa_full;           // pairs (leader): the odd CTA's query tile landed
 };
 
 __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
@@ -81,12 +83,17 @@ struct Item {
     int64_t row_begin, row_end;
 };
 
-__device__ __forceinline__ Item decode(const CallView& call, int64_t item) {
+// An item is (unit, row chunk), units numbered fastest. A unit is one query
+// tile, or with pairs of CTAs two query tiles, this CTA's being 2u + rank (a
+// pair's second tile may lie past the segment's queries: then every query of
+// it is invalid and only the other tile's results are kept).
+__device__ __forceinline__ Item decode(const CallView& call, int64_t item, uint32_t rank, bool pair) {
     Item it;
     it.p = call.plan[find_plan(call.plan, call.n_seg, item)];
     const int64_t local = item - it.p.item0;
-    it.chunk = (int)(local / it.p.qtiles);
-    it.qtile = (int)(local % it.p.qtiles);
+    it.chunk = (int)(local / it.p.units);
+    const int u = (int)(local % it.p.units);
+    it.qtile = pair ? 2 * u + (int)rank : u;
     it.qbase = it.p.q0 + it.qtile * BM;
     it.nq_tile = min(BM, it.p.nq - it.qtile * BM);
     it.row_begin = it.p.row0 + (int64_t)it.chunk * it.p.chunk_rows;
@@ -102,7 +109,14 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
         if (globaltimer() - t0 > kWaitLimitNs) break;
 }
 
-template <bool FP8, int LT>
+// PAIR: a cluster of two CTAs shares every tile (cta_group::2). Each CTA
+// loads its own 128 queries and its own half (128 rows) of each tile's rows;
+// the even CTA ("leader") issues M = 256 MMAs over both, and each CTA's
+// tensor memory receives its queries' 128 x 256 scores. The odd CTA's warp 1
+// forwards the completion of its loads to the leader's barriers; the
+// leader's commits reach the barriers of both CTAs; the odd CTA's epilogue
+// frees an accumulator with an arrival on the leader's barrier.
+template <bool FP8, int LT, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
           const __grid_constant__ CUtensorMap map_x, int kblocks, int stages) {
@@ -117,17 +131,26 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     const uint32_t a_smem = base;
     const uint32_t b_smem = a_smem + kblocks * kABlockBytes;
     constexpr int kElemsPerKBlock = FP8 ? 128 : 64;
-    const uint32_t idesc = FP8 ? instr_desc(0, BM, BN) : instr_desc(1, BM, BN);
+    constexpr uint32_t kBStage = PAIR ? kStageBytes / 2 : kStageBytes;   // bytes this CTA loads
+    constexpr uint32_t kM = PAIR ? 2 * BM : BM;
+    const uint32_t idesc = FP8 ? instr_desc(0, kM, BN) : instr_desc(1, kM, BN);
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int64_t unit0 = PAIR ? blockIdx.x / 2 : blockIdx.x;
+    const int64_t nunits = PAIR ? gridDim.x / 2 : gridDim.x;
+    constexpr uint16_t kPairMask = 0x3;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_u32(&bars.full[s]), 1);
             mbar_init(smem_u32(&bars.empty[s]), 1);
+            mbar_init(smem_u32(&bars.pfull[s]), 1);
         }
+        mbar_init(smem_u32(&bars.pa_full), 1);
         for (int a = 0; a < kAccs; ++a) {
             mbar_init(smem_u32(&bars.tmem_full[a]), 1);
-            mbar_init(smem_u32(&bars.tmem_empty[a]), kEpiThreads);
+            mbar_init(smem_u32(&bars.tmem_empty[a]), (PAIR ? 2 : 1) * kEpiWarps);
         }
         mbar_init(smem_u32(&bars.a_full), 1);
         mbar_init(smem_u32(&bars.a_empty), 1);
@@ -135,9 +158,16 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         for (int a = 0; a < kAccs; ++a) mbar_init(smem_u32(&bars.sx_ready[a]), kEpiThreads);
         fence_barrier_init();
     }
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), kTmemCols);
+    if (warp == 0) {
+        if (PAIR)
+            tmem_alloc_pair(smem_u32(&tmem_holder), kTmemCols);
+        else
+            tmem_alloc(smem_u32(&tmem_holder), kTmemCols);
+    }
     tc_fence_before();
     __syncthreads();
+    // the peer's barriers are initialised before any arrival can reach them
+    if (PAIR) cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = tmem_holder;
 
@@ -148,9 +178,8 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             prefetch_tensormap(&map_x);
             uint32_t it = 0, ic = 0, a_loads = 0;
             bool ok = true;
-            for (int64_t item = blockIdx.x; ok && item < call.total_items;
-                 item += gridDim.x, ++ic) {
-                const Item w = decode(call, item);
+            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
+                const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag);
                 if (!ok) break;
                 mbar_arrive_expect_tx(smem_u32(&bars.a_full), kblocks * kABlockBytes);
@@ -159,13 +188,15 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                 kb * kElemsPerKBlock, w.qbase);
                 ++a_loads;
                 for (int t = 0; ok && t < w.ntiles; ++t) {
-                    const int32_t row = (int32_t)(w.row_begin + (int64_t)t * BN);
+                    // this CTA's rows of the tile: all 256, or its half of them
+                    const int32_t row =
+                        (int32_t)(w.row_begin + (int64_t)t * BN + (PAIR ? rank * (BN / 2) : 0));
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
                         ok = mbar_wait(smem_u32(&bars.empty[s]), ph ^ 1, &abort_flag);
                         if (!ok) break;
-                        mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kStageBytes);
-                        tma_load_2d(b_smem + s * kStageBytes, &map_x, smem_u32(&bars.full[s]),
+                        mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kBStage);
+                        tma_load_2d(b_smem + s * kBStage, &map_x, smem_u32(&bars.full[s]),
                                     kb * kElemsPerKBlock, row);
                     }
                 }
@@ -177,15 +208,21 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (a_loads > 0) drain_wait(smem_u32(&bars.a_full), (a_loads - 1) & 1);
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 && (!PAIR || leader)) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t it = 0, tcount = 0, ic = 0;
             bool ok = true;
-            for (int64_t item = blockIdx.x; ok && item < call.total_items;
-                 item += gridDim.x, ++ic) {
-                const Item w = decode(call, item);
+            auto commit = [&](uint64_t& bar) {
+                if (PAIR)
+                    mma_commit_pair(smem_u32(&bar), kPairMask);
+                else
+                    mma_commit(smem_u32(&bar));
+            };
+            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
+                const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
+                if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pa_full), ic & 1, &abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 for (int t = 0; ok && t < w.ntiles; ++t, ++tcount) {
@@ -197,27 +234,59 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
                         ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
+                        if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pfull[s]), ph, &abort_flag);
                         if (!ok) break;
                         tc_fence_after();
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
                             const uint64_t ad =
                                 sw128_kmajor_desc(a_smem + kb * kABlockBytes + ks * 32);
-                            const uint64_t bd =
-                                sw128_kmajor_desc(b_smem + s * kStageBytes + ks * 32);
-                            if (FP8)
-                                mma_f8(d, ad, bd, idesc, (kb | ks) != 0);
-                            else
-                                mma_f16(d, ad, bd, idesc, (kb | ks) != 0);
+                            const uint64_t bd = sw128_kmajor_desc(b_smem + s * kBStage + ks * 32);
+                            if (PAIR) {
+                                if (FP8)
+                                    mma_f8_pair(d, ad, bd, idesc, (kb | ks) != 0);
+                                else
+                                    mma_f16_pair(d, ad, bd, idesc, (kb | ks) != 0);
+                            } else {
+                                if (FP8)
+                                    mma_f8(d, ad, bd, idesc, (kb | ks) != 0);
+                                else
+                                    mma_f16(d, ad, bd, idesc, (kb | ks) != 0);
+                            }
                         }
-                        mma_commit(smem_u32(&bars.empty[s]));
+                        commit(bars.empty[s]);
                     }
-                    if (ok) mma_commit(smem_u32(&bars.tmem_full[acc]));
+                    if (ok) commit(bars.tmem_full[acc]);
                 }
-                if (ok) mma_commit(smem_u32(&bars.a_empty));
+                if (ok) commit(bars.a_empty);
             }
             // every MMA this thread issued has finished before TMEM is freed
-            mma_commit(smem_u32(&bars.drain));
+            commit(bars.drain);
+            drain_wait(smem_u32(&bars.drain), 0);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ load forwarder
+        // (odd CTA of a pair) its query tile and ring slots landing, passed on
+        // to the leader's barriers in the order the leader consumes them
+        if (lane == 0) {
+            const uint32_t r_pa_full = mapa_shared(smem_u32(&bars.pa_full), 0);
+            uint32_t it = 0, ic = 0;
+            bool ok = true;
+            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
+                const Item w = decode(call, item, rank, PAIR);
+                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
+                if (!ok) break;
+                mbar_arrive_cluster(r_pa_full);
+                for (int t = 0; ok && t < w.ntiles; ++t) {
+                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                        const uint32_t s = it % stages, ph = (it / stages) & 1;
+                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
+                        if (!ok) break;
+                        mbar_arrive_cluster(mapa_shared(smem_u32(&bars.pfull[s]), 0));
+                    }
+                }
+            }
+            // the leader's last commit: every MMA writing this CTA's TMEM is done
             drain_wait(smem_u32(&bars.drain), 0);
         }
     } else {
@@ -229,8 +298,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         constexpr int kHalfCols = BN / 2;
         uint32_t tcount = 0;
         bool ok = true;
-        for (int64_t item = blockIdx.x; ok && item < call.total_items; item += gridDim.x) {
-            const Item w = decode(call, item);
+        // the barrier that frees an accumulator: the leader's
+        const uint32_t r_tmem_empty0 =
+            PAIR ? mapa_shared(smem_u32(&bars.tmem_empty[0]), 0) : smem_u32(&bars.tmem_empty[0]);
+        for (int64_t item = unit0; ok && item < call.total_items; item += nunits) {
+            const Item w = decode(call, item, rank, PAIR);
             const bool qvalid = lq < w.nq_tile;
             const int excl = (call.exclude && qvalid) ? call.exclude[w.qbase + lq] : -1;
             const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
@@ -342,7 +414,14 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     __syncwarp();
                 }
                 tc_fence_before();
-                mbar_arrive(smem_u32(&bars.tmem_empty[acc]));
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t bar = r_tmem_empty0 + acc * (uint32_t)sizeof(uint64_t);
+                    if (PAIR && !leader)
+                        mbar_arrive_cluster(bar);
+                    else
+                        mbar_arrive(bar);
+                }
                 if (qvalid && offered && st.cnt >= w.p.k) {
                     const float kth = st.kth_score(w.p.k);
                     // rounded down: the bound may only err low
@@ -366,9 +445,14 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     if (abort_flag && threadIdx.x == 0) atomicOr(db.status, kStTimeout);
     tc_fence_before();
     __syncthreads();
+    // no arrival or MMA of one CTA of a pair may reach the other after it exits
+    if (PAIR) cluster_sync();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        if (PAIR)
+            tmem_dealloc_pair(tmem_base, kTmemCols);
+        else
+            tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -388,21 +472,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 // Dynamic shared memory of a launch: the alignment slack, the query tile
-// (kblocks K blocks) and `stages` ring slots.
-size_t scan_tc_smem_bytes(int kblocks, int stages) {
-    return 1024 + (size_t)kblocks * kABlockBytes + (size_t)stages * kStageBytes;
+// (kblocks K blocks) and `stages` ring slots (half a tile's rows per slot
+// with pairs of CTAs).
+size_t scan_tc_smem_bytes(int kblocks, int stages, bool pair) {
+    return 1024 + (size_t)kblocks * kABlockBytes +
+           (size_t)stages * (pair ? kStageBytes / 2 : kStageBytes);
 }
 
 // As many ring slots as fit next to the query tile and the static shared
 // memory (barriers, FP8 scale staging), between 2 and kMaxStages.
-int scan_tc_stages(int kblocks, bool fp8) {
+int scan_tc_stages(int kblocks, bool fp8, bool pair) {
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 232448;
     const size_t static_bytes = sizeof(Bars) + 64 + (fp8 ? kAccs * BN * sizeof(float) : 0);
     const long avail = (long)optin - (long)static_bytes - 1024 - (long)kblocks * kABlockBytes;
-    int st = (int)(avail / (long)kStageBytes);
+    int st = (int)(avail / (long)(pair ? kStageBytes / 2 : kStageBytes));
     return st < 2 ? 2 : (st > kMaxStages ? kMaxStages : st);
 }
 
@@ -423,38 +509,105 @@ cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int c
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <bool FP8, int LT>
-cudaError_t launch_variant(const DbView& db, const CallView& call, const CUtensorMap& map_q,
-                           const CUtensorMap& map_x, int grid, int kblocks, cudaStream_t st) {
+template <bool FP8, int LT, bool PAIR>
+cudaError_t set_smem(size_t smem) {
     static size_t attr_bytes = 0;   // the largest dynamic size set so far
-    const int stages = scan_tc_stages(kblocks, FP8);
-    const size_t smem = scan_tc_smem_bytes(kblocks, stages);
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_scan_tc<FP8, LT>,
+        cudaError_t e = cudaFuncSetAttribute(k_scan_tc<FP8, LT, PAIR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    k_scan_tc<FP8, LT><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks, stages);
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+template <bool FP8, int LT, bool PAIR>
+cudaError_t launch_variant(const DbView& db, const CallView& call, const CUtensorMap& map_q,
+                           const CUtensorMap& map_x, int grid, int kblocks, cudaStream_t st) {
+    const int stages = scan_tc_stages(kblocks, FP8, PAIR);
+    const size_t smem = scan_tc_smem_bytes(kblocks, stages, PAIR);
+    cudaError_t e = set_smem<FP8, LT, PAIR>(smem);
+    if (e != cudaSuccess) return e;
+    if (!PAIR) {
+        k_scan_tc<FP8, LT, false><<<grid, kThreads, smem, st>>>(db, call, map_q, map_x, kblocks,
+                                                                 stages);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_scan_tc<FP8, LT, PAIR>, db, call, map_q, map_x, kblocks,
+                              stages);
+}
+
+template <bool PAIR>
+cudaError_t launch_lists(bool fp8, int list_t, const DbView& db, const CallView& call,
+                         const CUtensorMap& map_q, const CUtensorMap& map_x, int grid, int kblocks,
+                         cudaStream_t st) {
+    if (list_t == kListTTiny)
+        return fp8 ? launch_variant<true, kListTTiny, PAIR>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListTTiny, PAIR>(db, call, map_q, map_x, grid, kblocks, st);
+    if (list_t == kListTSmall)
+        return fp8 ? launch_variant<true, kListTSmall, PAIR>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListTSmall, PAIR>(db, call, map_q, map_x, grid, kblocks, st);
+    if (list_t == kListT)
+        return fp8 ? launch_variant<true, kListT, PAIR>(db, call, map_q, map_x, grid, kblocks, st)
+                   : launch_variant<false, kListT, PAIR>(db, call, map_q, map_x, grid, kblocks, st);
+    return cudaErrorInvalidValue;
+}
+
+// Pairs of CTAs that can be resident at once (a cluster occupies two SMs of
+// one GPU processing cluster; not every SM need find a partner), 0 on error.
+int scan_tc_pair_slots(bool fp8, int kblocks) {
+    static int cached[2][kMaxKBlocks + 1] = {};
+    if (kblocks < 1 || kblocks > kMaxKBlocks) return 0;
+    int& c = cached[fp8 ? 1 : 0][kblocks];
+    if (c > 0) return c;
+    const int stages = scan_tc_stages(kblocks, fp8, true);
+    const size_t smem = scan_tc_smem_bytes(kblocks, stages, true);
+    cudaError_t e = fp8 ? set_smem<true, kListTSmall, true>(smem) : set_smem<false, kListTSmall, true>(smem);
+    if (e != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    e = fp8 ? cudaOccupancyMaxActiveClusters(&n, k_scan_tc<true, kListTSmall, true>, &cfg)
+            : cudaOccupancyMaxActiveClusters(&n, k_scan_tc<false, kListTSmall, true>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    c = n;
+    return c;
 }
 
 cudaError_t launch_scan_tc(const DbView& db, const CallView& call, const CUtensorMap& map_q,
-                           const CUtensorMap& map_x, int grid, int list_t, cudaStream_t st) {
+                           const CUtensorMap& map_x, int grid, int list_t, bool pair,
+                           cudaStream_t st) {
     if (call.total_items == 0) return cudaSuccess;
     const bool fp8 = db.prec == FS_FP8_E4M3;
     const int kblocks = (int)(db.fl * (fp8 ? 1 : 2) / 128);
     if (kblocks < 1 || kblocks > kMaxKBlocks) return cudaErrorInvalidValue;
-    if (list_t == kListTTiny)
-        return fp8 ? launch_variant<true, kListTTiny>(db, call, map_q, map_x, grid, kblocks, st)
-                   : launch_variant<false, kListTTiny>(db, call, map_q, map_x, grid, kblocks, st);
-    if (list_t == kListTSmall)
-        return fp8 ? launch_variant<true, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st)
-                   : launch_variant<false, kListTSmall>(db, call, map_q, map_x, grid, kblocks, st);
-    if (list_t == kListT)
-        return fp8 ? launch_variant<true, kListT>(db, call, map_q, map_x, grid, kblocks, st)
-                   : launch_variant<false, kListT>(db, call, map_q, map_x, grid, kblocks, st);
-    return cudaErrorInvalidValue;
+    if (pair && (grid & 1)) return cudaErrorInvalidValue;
+    return pair ? launch_lists<true>(fp8, list_t, db, call, map_q, map_x, grid, kblocks, st)
+                : launch_lists<false>(fp8, list_t, db, call, map_q, map_x, grid, kblocks, st);
 }
 
 }  // namespace fsk
