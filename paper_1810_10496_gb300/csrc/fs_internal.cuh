@@ -60,35 +60,43 @@ __device__ __forceinline__ int32_t key_index(uint64_t key) {
     return (int32_t)(0xffffffffu - (uint32_t)key);
 }
 
-// One thread's candidate list, held in registers: its LT best keys in
-// descending order, zeros while filling (every index is a compile-time
-// constant, so the array never leaves the register file). A key is inserted
-// by one compare-and-exchange pass; the lowest kept key is always the last.
+// One thread's candidate list, held in registers: its LT best scores in
+// descending order with their segment-local rows (-inf while filling; every
+// index is a compile-time constant, so the arrays never leave the register
+// file). A candidate is inserted by one compare-exchange pass over 32-bit
+// scores; the lowest kept score is always the last. A score equal to the
+// lowest kept one is not inserted: rows arrive in increasing order, so the
+// earlier, lower row stays. The 64-bit keys of the merge are formed on output.
 template <int LT>
 struct RegList {
-    uint64_t k[LT];
-    uint64_t thr_key;  // lowest key kept once the list is full (0 before)
-    float thr_s;       // its score; -inf while the list is filling
-    int cnt;           // keys stored so far (at most LT)
+    float s[LT];
+    uint32_t r[LT];
+    float thr_s;       // lowest kept score once the list is full; -inf before
+    int cnt;           // entries stored so far (at most LT)
 
     __device__ __forceinline__ void reset() {
 #pragma unroll
-        for (int e = 0; e < LT; ++e) k[e] = 0;
-        thr_key = 0;
+        for (int e = 0; e < LT; ++e) {
+            s[e] = -INFINITY;
+            r[e] = 0;
+        }
         thr_s = -INFINITY;
         cnt = 0;
     }
 
-    // Score of the kk-th best key held (1 <= kk <= cnt): the least of the
+    // Score of the kk-th best entry held (1 <= kk <= cnt): the least of the
     // first kk, taken as a minimum so that no index is computed at run time.
     __device__ __forceinline__ float kth_score(int kk) const {
-        uint64_t t = ~0ull;
+        float t = INFINITY;
 #pragma unroll
-        for (int e = 0; e < LT; ++e) {
-            const uint64_t c = e < kk ? k[e] : ~0ull;
-            t = c < t ? c : t;
-        }
-        return key_score(t);
+        for (int e = 0; e < LT; ++e)
+            if (e < kk) t = fminf(t, s[e]);
+        return t;
+    }
+
+    // The merge key of entry e (0 for an empty entry).
+    __device__ __forceinline__ uint64_t key(int e) const {
+        return cnt > e ? make_key(s[e], r[e]) : 0ull;
     }
 
     // Offers (score, row): kept if the list is filling or it beats the lowest.
@@ -96,20 +104,21 @@ struct RegList {
                                           int excl) {
         const int32_t li = (int32_t)(row - row0);
         if (row >= row_end || li == excl) return;
-        uint64_t x = make_key(v, (uint32_t)li);
-        if (x <= thr_key) return;
+        if (!(v > thr_s)) return;
+        float x = v;
+        uint32_t xi = (uint32_t)li;
 #pragma unroll
         for (int e = 0; e < LT; ++e) {
-            const uint64_t a = k[e];
+            const float a = s[e];
+            const uint32_t ai = r[e];
             const bool up = x > a;
-            k[e] = up ? x : a;
+            s[e] = up ? x : a;
+            r[e] = up ? xi : ai;
             x = up ? a : x;
+            xi = up ? ai : xi;
         }
         cnt += cnt < LT ? 1 : 0;
-        if (k[LT - 1] != 0) {
-            thr_key = k[LT - 1];
-            thr_s = key_score(thr_key);
-        }
+        if (cnt == LT) thr_s = s[LT - 1];
     }
 };
 #endif

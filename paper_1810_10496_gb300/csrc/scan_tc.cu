@@ -437,7 +437,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 uint64_t* dst = call.cand + w.p.cand0 +
                                 ((qlocal * w.p.chunks + w.chunk) * 2 + half) * (int64_t)LT;
 #pragma unroll
-                for (int e = 0; e < LT; ++e) dst[e] = st.k[e];
+                for (int e = 0; e < LT; ++e) dst[e] = st.key(e);
             }
         }
     }

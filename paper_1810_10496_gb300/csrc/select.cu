@@ -418,7 +418,7 @@ k_fb_scan32(DbView db, CallView call) {
         }
         if (lane == 0) {
 #pragma unroll
-            for (int e = 0; e < kListT; ++e) wl[wid][e] = lst.k[e];
+            for (int e = 0; e < kListT; ++e) wl[wid][e] = lst.key(e);
         }
         __syncthreads();
         if (wid == 0) {
