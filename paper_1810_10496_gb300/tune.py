@@ -29,10 +29,10 @@ L2_SHARE_PCT = (25, 50, -1)
 
 
 def candidates(prec: str, n_seg: int, k_max: int) -> list[dict]:
-    """The tunings worth timing for this shape: the list length matters only
-    for the tensor-core scans with every k <= 8, the L2 share only for a
+    """The tunings worth timing for this shape: the list length (each that
+    holds k) matters only for the tensor-core scans, the L2 share only for a
     single segment. The defaults come first."""
-    lists = tuple(n for n in LIST_LEN if n >= k_max and n < 16) if prec != "fp32" else ()
+    lists = tuple(n for n in LIST_LEN if n >= k_max) if prec != "fp32" else ()
     lists = lists or (0,)
     shares = L2_SHARE_PCT if n_seg == 1 else (0,)
     out = [{"items_per_block": 0, "list_len": 0, "l2_share_pct": 0}]

@@ -13,15 +13,15 @@ def test_candidates_shape_rules():
     # every distinct (items, list, share) once, the default not repeated
     norm = [tune._normal(c, "bf16", 3) for c in bf]
     assert len(norm) == len(set(norm))
-    # list lengths 4 and 8 (16 is never better when every k fits in 8)
-    assert len(bf) == len(tune.ITEMS_PER_BLOCK) * 2 * len(tune.L2_SHARE_PCT)
-    assert {c["list_len"] for c in bf} == {0, 4, 8}
+    # list lengths 4, 8 and 16
+    assert len(bf) == len(tune.ITEMS_PER_BLOCK) * 3 * len(tune.L2_SHARE_PCT)
+    assert {c["list_len"] for c in bf} == {0, 4, 8, 16}
     # k = 5: lists of 4 cannot hold the answer
-    assert {c["list_len"] for c in tune.candidates("bf16", 1, 5)} == {0, 8}
+    assert {c["list_len"] for c in tune.candidates("bf16", 1, 5)} == {0, 8, 16}
     # several segments: no L2 share; k > 8 or FP32: no list length
     multi = tune.candidates("bf16", 512, 3)
     assert {c["l2_share_pct"] for c in multi} == {0}
-    assert {c["list_len"] for c in tune.candidates("bf16", 1, 16)} == {0}
+    assert {c["list_len"] for c in tune.candidates("bf16", 1, 16)} == {0, 16}
     assert {c["list_len"] for c in tune.candidates("fp32", 1, 3)} == {0}
 
 
