@@ -207,14 +207,27 @@ k_scan_fp32(DbView db, CallView call) {
             }
         }
 
-        // publish this item's lists
+        // publish this item's lists, sorted in descending order (empty entries,
+        // 0, last) as the selection expects: an odd-even transposition sort
         if (lq < nq_tile) {
             const int64_t qlocal = (int64_t)qtile * BQ + lq;
             uint64_t* dst = call.cand + p.cand0 +
                             ((qlocal * p.chunks + chunk) * p.lists + hf) * (int64_t)T;
             // (this kernel always keeps lists of kListT = T entries)
+            uint64_t v[T];
 #pragma unroll
-            for (int e = 0; e < T; ++e) dst[e] = sm.lists[e][tid];
+            for (int e = 0; e < T; ++e) v[e] = sm.lists[e][tid];
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+#pragma unroll
+                for (int e = r & 1; e + 1 < T; e += 2) {
+                    const uint64_t a = v[e], b = v[e + 1];
+                    v[e] = a > b ? a : b;
+                    v[e + 1] = a > b ? b : a;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < T; ++e) dst[e] = v[e];
         }
         __syncthreads();  // s_item and the lists are reused by the next item
     }

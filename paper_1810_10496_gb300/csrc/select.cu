@@ -118,6 +118,7 @@ __device__ __forceinline__ void write_padding(const CallView& call, int q, int f
 }
 
 constexpr int kSelWarps = 8;
+constexpr int kRescoreRows = 4;   // window rows the FP32 rescoring reads at once
 
 struct SelShared {
     int32_t widx[kSelWarps][kWindow];     // window rows (segment-local), scan order
@@ -155,7 +156,8 @@ __device__ double exact_norm2(const float* __restrict__ q, int f) {
     return a;
 }
 
-// Answers query q from its candidate lists: cand holds nl lists of lt keys,
+// Answers query q from its candidate lists: cand holds nl lists of lt keys
+// (each sorted, descending, empty entries last),
 // every approximate score within E of the exact cosine. Returns the number of
 // places written, or -1 when the lists do not certify the answer (nothing is
 // written then). Whole warp.
@@ -166,14 +168,23 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     const int64_t out0 = (int64_t)q * call.k_max;
     const int64_t ne = (int64_t)nl * lt;
 
-    // 1. k-th best approximate key
+    // Every list is sorted: its keys in descending order, empty entries (0)
+    // last. So the k best keys overall are among the first k of each list, a
+    // full list's lowest key is its last, and the entries of a list that can
+    // reach the top k form a prefix of it.
+    const int kk = k < lt ? k : lt;
+
+    // 1. k-th best approximate key (rounds after the first read L1)
     uint64_t prev = ~0ull, kth = 0;
     int ntop = 0;
     for (int r = 0; r < k; ++r) {
         uint64_t best = 0;
-        for (int64_t e = lane; e < ne; e += 32) {
-            uint64_t v = cand[e];
-            if (v < prev && v > best) best = v;
+        for (int l = lane; l < nl; l += 32) {
+            const uint64_t* L = cand + (int64_t)l * lt;
+            for (int e = 0; e < kk; ++e) {
+                const uint64_t v = L[e];
+                if (v < prev && v > best) best = v;
+            }
         }
         best = warp_max_u64(best);
         if (best == 0) break;
@@ -185,29 +196,30 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     // 2. certification against the lowest kept key of every full list
     uint64_t tau = 0;
     for (int l = lane; l < nl; l += 32) {
-        uint64_t mn = ~0ull;
-        for (int e = 0; e < lt; ++e) {
-            uint64_t v = cand[(int64_t)l * lt + e];
-            mn = v < mn ? v : mn;
-        }
-        if (mn != 0) tau = mn > tau ? mn : tau;   // full list
+        const uint64_t v = cand[(int64_t)l * lt + lt - 1];   // 0 unless the list is full
+        tau = v > tau ? v : tau;
     }
     tau = warp_max_u64(tau);
     const double tk = ntop ? (double)key_score(kth) : -INFINITY;
     bool certified = (tau == 0) || ((double)key_score(tau) + 2.0 * E < tk);
 
-    // 3. window of candidates that can still reach the top k
+    // 3. window of candidates that can still reach the top k: a lane per list,
+    //    entry by entry until no list has one left
     int nw = 0;
     if (certified && ntop > 0) {
         const double lo = tk - 2.0 * E;
-        for (int64_t e0 = 0; e0 < ne; e0 += 32) {
-            const int64_t e = e0 + lane;
-            uint64_t v = e < ne ? cand[e] : 0;
-            bool in = v != 0 && (double)key_score(v) >= lo;
-            unsigned m = __ballot_sync(kFull, in);
-            int pos = nw + __popc(m & ((1u << lane) - 1));
-            if (in && pos < kWindow) sh.widx[wid][pos] = key_index(v);
-            nw += __popc(m);
+        for (int l0 = 0; l0 < nl; l0 += 32) {
+            const int l = l0 + lane;
+            const uint64_t* L = cand + (int64_t)l * lt;
+            for (int e = 0; e < lt; ++e) {
+                const uint64_t v = l < nl ? L[e] : 0;
+                const bool in = v != 0 && (double)key_score(v) >= lo;
+                const unsigned m = __ballot_sync(kFull, in);
+                if (m == 0) break;
+                const int pos = nw + __popc(m & ((1u << lane) - 1));
+                if (in && pos < kWindow) sh.widx[wid][pos] = key_index(v);
+                nw += __popc(m);
+            }
         }
         if (nw > kWindow) certified = false;
     }
@@ -216,26 +228,38 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
 
     // 4. FP32 rescoring of the window: the cosine of the unit vectors and
     //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
+    //    (kRescoreRows window rows per pass, so their loads overlap)
     const float* qu = call.q_unit + (int64_t)q * db.fu;
-    for (int w = 0; w < nw; ++w) {
-        const int64_t row = p.row0 + sh.widx[wid][w];
-        const float* xu = db.unit + row * (int64_t)db.fu;
-        float dot = 0.0f, dd = 0.0f;
-        for (int i = lane; i < db.fu; i += 32) {
-            const float a = qu[i], b = xu[i];
-            dot = fmaf(a, b, dot);
-            const float t = a - b;
-            dd = fmaf(t, t, dd);
+    for (int w0 = 0; w0 < nw; w0 += kRescoreRows) {
+        float dot[kRescoreRows], dd[kRescoreRows];
+        int64_t row[kRescoreRows];
+#pragma unroll
+        for (int j = 0; j < kRescoreRows; ++j) {
+            dot[j] = 0.0f;
+            dd[j] = 0.0f;
+            row[j] = w0 + j < nw ? p.row0 + sh.widx[wid][w0 + j] : -1;
+            if (row[j] >= 0) {
+                const float* xu = db.unit + row[j] * (int64_t)db.fu;
+                for (int i = lane; i < db.fu; i += 32) {
+                    const float a = qu[i], b = xu[i];
+                    dot[j] = fmaf(a, b, dot[j]);
+                    const float t = a - b;
+                    dd[j] = fmaf(t, t, dd[j]);
+                }
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dot += __shfl_xor_sync(kFull, dot, o);
-            dd += __shfl_xor_sync(kFull, dd, o);
-        }
-        if (lane == 0) {
-            sh.wsc[wid][w] = dot;
-            // a zero row has cosine 0 by convention: d = 1
-            sh.wdist[wid][w] = db.b64[row] == 0.0 ? 1.0f : 0.5f * dd;
+        for (int j = 0; j < kRescoreRows; ++j) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dot[j] += __shfl_xor_sync(kFull, dot[j], o);
+                dd[j] += __shfl_xor_sync(kFull, dd[j], o);
+            }
+            if (lane == 0 && row[j] >= 0) {
+                sh.wsc[wid][w0 + j] = dot[j];
+                // a zero row has cosine 0 by convention: d = 1
+                sh.wdist[wid][w0 + j] = db.b64[row[j]] == 0.0 ? 1.0f : 0.5f * dd[j];
+            }
         }
     }
     __syncwarp();
@@ -391,6 +415,8 @@ k_select(DbView db, CallView call) {
 
 constexpr int kFbThreads = 256;
 constexpr int kFbWarps = kFbThreads / 32;
+constexpr int kFbRows = 4;     // rows a warp scores per pass
+constexpr int kGatherPerWarp = 4;   // (query, slot) pairs a warp gathers
 
 __global__ void __launch_bounds__(kFbThreads)
 k_fb_scan32(DbView db, CallView call) {
@@ -407,14 +433,28 @@ k_fb_scan32(DbView db, CallView call) {
         const float* qu = call.q_unit + (int64_t)q * db.fu;
         RegList<kListT> lst;
         lst.reset();
-        for (int64_t row = lo + wid; row < hi; row += kFbWarps) {
-            const float* xu = db.unit + row * (int64_t)db.fu;
-            float dot = 0.0f;
-            for (int i = lane; i < db.fu; i += 32) dot = fmaf(qu[i], xu[i], dot);
+        // kFbRows rows per pass, so their loads are in flight together
+        for (int64_t row0 = lo + (int64_t)wid * kFbRows; row0 < hi; row0 += kFbWarps * kFbRows) {
+            float dot[kFbRows];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
-            dot = __shfl_sync(kFull, dot, 0);   // the same value (lane 0's sum) in every lane
-            if (lst.cnt < kListT || dot >= lst.thr_s) lst.offer(dot, row, hi, p.row0, excl);
+            for (int r = 0; r < kFbRows; ++r) {
+                dot[r] = 0.0f;
+                if (row0 + r < hi) {
+                    const float* xu = db.unit + (row0 + r) * (int64_t)db.fu;
+                    for (int i = lane; i < db.fu; i += 32) dot[r] = fmaf(qu[i], xu[i], dot[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kFbRows; ++r) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dot[r] += __shfl_xor_sync(kFull, dot[r], o);
+                // the same value (lane 0's sum) in every lane
+                dot[r] = __shfl_sync(kFull, dot[r], 0);
+            }
+#pragma unroll
+            for (int r = 0; r < kFbRows; ++r)
+                if (row0 + r < hi && (lst.cnt < kListT || dot[r] >= lst.thr_s))
+                    lst.offer(dot[r], row0 + r, hi, p.row0, excl);
         }
         if (lane == 0) {
 #pragma unroll
@@ -595,11 +635,15 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
 // ---------------------------------------------------------------------------
 // gather of the neighbours' phase orders: one warp per (query, slot)
 
+// Eight lanes per (query, slot), four per warp, so four independent chains
+// of loads (result row, order offsets, pass IDs) are in flight per warp.
 __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out,
                          int32_t* __restrict__ seq_len, int l_max, int32_t* __restrict__ dup_of) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= (int64_t)call.nq * call.k_max) return;
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    const unsigned gmask = 0xffu << (grp * 8);
+    const int64_t w =
+        ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kGatherPerWarp + grp;
+    if (w >= (int64_t)call.nq * call.k_max) return;   // whole groups leave together
     const int q = (int)(w / call.k_max), c = (int)(w % call.k_max);
     const SegPlan p = call.plan[plan_of_query(call, q)];
     const int r = call.out_idx[w];
@@ -610,8 +654,8 @@ __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out
         len = db.seq_off[p.row0 + r + 1] - lo;
     }
     const int64_t m = len < l_max ? len : l_max;
-    for (int i = lane; i < l_max; i += 32) dst[i] = i < m ? db.seq_ids[lo + i] : (int16_t)-1;
-    if (lane == 0) seq_len[w] = (int32_t)len;
+    for (int i = sub; i < l_max; i += 8) dst[i] = i < m ? db.seq_ids[lo + i] : (int16_t)-1;
+    if (sub == 0) seq_len[w] = (int32_t)len;
     if (dup_of) {
         int first = -1;
         if (r >= 0) {
@@ -622,12 +666,12 @@ __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out
                 const int64_t len2 = db.seq_off[p.row0 + r2 + 1] - lo2;
                 if (len2 != len) continue;
                 bool same = true;
-                for (int64_t i = lane; i < len; i += 32)
+                for (int64_t i = sub; i < len; i += 8)
                     same &= db.seq_ids[lo + i] == db.seq_ids[lo2 + i];
-                if (__all_sync(kFull, same)) first = c2;
+                if (__all_sync(gmask, same)) first = c2;
             }
         }
-        if (lane == 0) dup_of[w] = first;
+        if (sub == 0) dup_of[w] = first;
     }
 }
 
@@ -659,7 +703,7 @@ cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t s
 
 cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms, cudaStream_t st) {
     if (call.nq == 0) return cudaSuccess;
-    k_fb_scan32<<<num_sms * 2, kFbThreads, 0, st>>>(db, call);
+    k_fb_scan32<<<num_sms * 4, kFbThreads, 0, st>>>(db, call);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     k_fb_select<<<num_sms, kSelWarps * 32, 0, st>>>(db, call);
@@ -674,8 +718,9 @@ cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
 
 cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_out, int32_t* seq_len,
                           int l_max, int32_t* dup_of, cudaStream_t st) {
-    const int64_t warps = (int64_t)call.nq * call.k_max;
-    if (warps == 0) return cudaSuccess;
+    const int64_t items = (int64_t)call.nq * call.k_max;
+    if (items == 0) return cudaSuccess;
+    const int64_t warps = ceil_div(items, kGatherPerWarp);
     k_gather<<<(unsigned)ceil_div(warps, 8), 256, 0, st>>>(db, call, seq_out, seq_len, l_max,
                                                             dup_of);
     return cudaGetLastError();
