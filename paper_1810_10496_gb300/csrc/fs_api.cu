@@ -175,20 +175,22 @@ Bounds score_bounds(const fs_db* db, double r_xmax) {
     Bounds b;
     b.rerank = gamma(m + 5) * U * U + e_norm;
     if (db->prec == FS_FP32) {
-        b.scan = gamma(db->fu) * U * U + e_norm;
+        b.scan = (gamma(db->fu) * U * U + e_norm) * 1.25 + 1e-12;
         b.rq = 0.0;
     } else {
         // low-precision codes c with ||u - c|| = r: |c_q.c_x - u_q.u_x| <=
-        // r_q (U + r_x) + U r_x; FP32 accumulation of exact products within
-        // 4 K u sum|p| (tensor cores may truncate); FP8 adds the two scale
-        // multiplications of the epilogue
+        // r_q (U + r_x) + U r_x by Cauchy-Schwarz. The residual norms are
+        // computed from the exact rounding errors with a sum of squares and a
+        // square root (relative error below 1e-6), so a 0.1 % margin covers
+        // them. The accumulation of the exact products in FP32 is allowed
+        // 8 K u sum|p|, twice the bound of an adder that truncates, for
+        // tensor-core accumulation of undocumented internal width; FP8 adds
+        // the two scale multiplications of the epilogue.
         const double cmax = U * (db->prec == FS_BF16 ? 1.004 : 1.1);
-        b.scan = U * r_xmax + 4.0 * db->fl * u * cmax * cmax + e_norm +
-                 (db->prec == FS_FP8_E4M3 ? 3.0 * u * cmax * cmax : 0.0);
-        b.rq = U + r_xmax;
+        b.scan = U * r_xmax * 1.001 + 8.0 * db->fl * u * cmax * cmax + e_norm * 1.25 +
+                 (db->prec == FS_FP8_E4M3 ? 6.0 * u * cmax * cmax : 0.0) + 1e-12;
+        b.rq = (U + r_xmax) * 1.001;
     }
-    b.scan = b.scan * 1.25 + 1e-12;
-    b.rq = b.rq * 1.25;
     b.rerank = b.rerank * 1.25 + 1e-12;
     return b;
 }
