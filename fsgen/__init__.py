@@ -173,3 +173,62 @@ def make(name: str, seed: int = 0, workers: int = 1, n: int | None = None,
     w.queries = query_rows(seed, w.q, w.f, workers)
     w.seq_off, w.seq_ids = phase_orders(seed, w.n)
     return w
+
+
+STREAM_DSE = 5
+
+
+@dataclass
+class DseSuite:
+    """A synthetic reference set for the evaluation procedure of Sec. 4.2:
+    kernels with feature vectors, each kernel's best phase order, and the
+    speedup of every kernel compiled with every kernel's best order."""
+    features: np.ndarray        # [n][f] float32 counts
+    seq_off: np.ndarray         # [n + 1] int64 CSR offsets of the best orders
+    seq_ids: np.ndarray         # int16 pass IDs
+    speedup: np.ndarray         # [n][n] float64: kernel i compiled with order j
+    family: np.ndarray          # [n] int64 family label of each kernel
+
+
+def dse_suite(seed: int = 0, n: int = 15, f: int = 55, families: int = 5,
+              duplicate_orders: int = 2) -> DseSuite:
+    """Kernels drawn in `families` families (the stand-in for the paper's 15
+    PolyBench/GPU kernels and Table 1): a family has an opcode mix and a best
+    phase order; a member's features are ``rint(total * mix')`` with ``mix'``
+    drawn close to the family mix, and its best order is the family order
+    with a few passes replaced. Speedups (over compilation without phase
+    ordering, the fallback) are lognormal draws: around 1.5 for an order
+    from the kernel's own family, around 1.0 otherwise (below 1 is a
+    slowdown), and the kernel's own order is the best of its row.
+    `duplicate_orders` kernels reuse another kernel's order exactly, as
+    Table 1 repeats some orders. Drawn from family labels alone: there is no
+    similarity arithmetic here."""
+    rng = np.random.default_rng([seed, STREAM_DSE, 0])
+    fam = rng.integers(0, families, size=n).astype(np.int64)
+    fam_mix = rng.dirichlet(np.full(f, 0.3), size=families)
+    fam_len = rng.integers(8, 48, size=families)
+    fam_order = [rng.integers(0, N_PASSES, size=int(fam_len[c])) for c in range(families)]
+    feats = np.zeros((n, f), dtype=np.float32)
+    orders = []
+    for i in range(n):
+        c = fam[i]
+        mix = rng.dirichlet(200.0 * fam_mix[c] + 1e-3)
+        total = rng.lognormal(mean=6.0, sigma=0.5)
+        feats[i] = np.rint(total * mix).astype(np.float32)
+        o = fam_order[c].copy()
+        edits = rng.integers(0, o.size, size=max(1, o.size // 8))
+        o[edits] = rng.integers(0, N_PASSES, size=edits.size)
+        orders.append(o.astype(np.int16))
+    for d in range(min(duplicate_orders, n - 1)):
+        orders[n - 1 - d] = orders[d].copy()
+    same = fam[:, None] == fam[None, :]
+    speed = np.where(same, rng.lognormal(np.log(1.5), 0.15, size=(n, n)),
+                     rng.lognormal(0.0, 0.25, size=(n, n)))
+    for i in range(n):
+        speed[i, i] = speed[i].max() * rng.uniform(1.0, 1.1)
+    # kernels sharing an order exactly get one speedup per (kernel, order)
+    for d in range(min(duplicate_orders, n - 1)):
+        speed[:, n - 1 - d] = speed[:, d]
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum([o.size for o in orders], out=off[1:])
+    return DseSuite(feats, off, np.concatenate(orders).astype(np.int16), speed, fam)

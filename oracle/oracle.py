@@ -49,7 +49,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["norm2", "dot_seq", "cosine_scores", "knn", "recommend", "gather",
-           "exact_integer_inputs"]
+           "exact_integer_inputs", "standardize_stats", "standardize", "metric_distances",
+           "knn_metric", "METRICS"]
 
 
 def norm2(x: np.ndarray) -> np.ndarray:
@@ -218,3 +219,74 @@ def knn_segments(x, queries, seg_off, q_seg_off, ks, **kw):
         qs = queries[q_seg_off[s]:q_seg_off[s + 1]]
         out.append(knn(xs, qs, int(ks[s]), **kw))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Other similarity metrics (Sec. 4.2 names their evaluation as future work;
+# these are the readings the library implements for it): Euclidean and
+# Manhattan distance between standardised feature vectors.
+#
+# 6. Standardisation statistics come from the reference set (one database
+#    segment), per feature f, in binary64 with the row order i = 0..n-1:
+#    ``mu_f = (sum_i x_if) / n`` and the population deviation
+#    ``sigma_f = sqrt((sum_i (x_if - mu_f)**2) / n)``, sums sequential, no
+#    fused multiply-add. ``z_f = (v_f - mu_f) / sigma_f`` for database rows
+#    and queries alike; a feature with ``sigma_f == 0`` (constant over the
+#    reference set) gives ``z_f = 0``.
+# 7. Euclidean: ``d = sqrt(sum_f (zq_f - zx_f)**2)``; Manhattan:
+#    ``d = sum_f |zq_f - zx_f|``; each sum sequential in f, binary64, no fused
+#    multiply-add. Ranking: d ascending, equal d to the lower index.
+
+METRICS = ("cosine", "euclidean", "manhattan")
+
+
+def standardize_stats(x: np.ndarray):
+    """Per-feature mean and population deviation of the rows of ``x``
+    (reading 6): ``(mu float64[f], sigma float64[f])``."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    if n == 0:
+        return np.zeros(x.shape[1]), np.zeros(x.shape[1])
+    # np.cumsum adds in order, so its last element is the sequential sum
+    mu = np.cumsum(x, axis=0)[-1] / n
+    d = x - mu
+    var = np.cumsum(d * d, axis=0)[-1] / n
+    return mu, np.sqrt(var)
+
+
+def standardize(v: np.ndarray, mu: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """``z = (v - mu) / sigma``, 0 where sigma is 0 (reading 6)."""
+    v = np.asarray(v, dtype=np.float64)
+    safe = np.where(sigma > 0, sigma, 1.0)
+    return np.where(sigma > 0, (v - mu) / safe, 0.0)
+
+
+def metric_distances(q: np.ndarray, x: np.ndarray, metric: str, mu, sigma) -> np.ndarray:
+    """``[nq, n]`` binary64 distances under ``metric`` (reading 7)."""
+    zq = standardize(q, mu, sigma)
+    zx = standardize(x, mu, sigma)
+    acc = np.zeros((zq.shape[0], zx.shape[0]), dtype=np.float64)
+    for f in range(zq.shape[1]):
+        diff = zq[:, f][:, None] - zx[:, f][None, :]
+        acc = acc + (diff * diff if metric == "euclidean" else np.abs(diff))
+    return np.sqrt(acc) if metric == "euclidean" else acc
+
+
+def knn_metric(x: np.ndarray, queries: np.ndarray, k: int, metric: str, exclude=None,
+               chunk: int = 16384):
+    """k nearest rows per query under ``metric`` (cosine goes to ``knn``):
+    ``(idx int64[nq, k], dist float64[nq, k])``, padded with -1 and +inf."""
+    if metric == "cosine":
+        i, d, _ = knn(x, queries, k, exclude=exclude)
+        return i, d
+    x = np.asarray(x, dtype=np.float64)
+    q = np.asarray(queries, dtype=np.float64)
+    mu, sigma = standardize_stats(x)
+    best_i = np.full((q.shape[0], k), -1, dtype=np.int64)
+    best_s = np.full((q.shape[0], k), -np.inf, dtype=np.float64)
+    for lo in range(0, x.shape[0], chunk):
+        hi = min(x.shape[0], lo + chunk)
+        s = -metric_distances(q, x[lo:hi], metric, mu, sigma)   # larger is nearer
+        ci, cs = _topk_rows(s, np.arange(lo, hi, dtype=np.int64), k, exclude)
+        best_i, best_s = _merge(best_i, best_s, ci, cs, k)
+    return best_i, np.where(best_i >= 0, -best_s, np.inf)

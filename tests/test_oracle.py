@@ -352,3 +352,112 @@ def test_planted_mistakes_are_caught(golden_dir):
         assert not _pins_pass(bad, _mk_knn(bad), golden_dir), bad.__name__
     assert not _pins_pass(good, _mk_knn(good, order="asc"), golden_dir)
     assert not _pins_pass(good, _mk_knn(good, tie="high"), golden_dir)
+
+
+# ---------------------------------------------------------------------------
+# other metrics (standardised Euclidean and Manhattan)
+
+def test_metric_closed_form_grid():
+    """Rows at the corners of a 2 x 2 grid: mu = (1, 1), sigma = (1, 1), so
+    z is the row minus (1, 1); the query (2, 0) sits on row 1."""
+    x = np.array([[0, 0], [2, 0], [0, 2], [2, 2]], dtype=np.float32)
+    mu, sigma = oracle.standardize_stats(x)
+    assert np.array_equal(mu, [1.0, 1.0]) and np.array_equal(sigma, [1.0, 1.0])
+    q = np.array([[2, 0]], dtype=np.float32)
+    de = oracle.metric_distances(q, x, "euclidean", mu, sigma)[0]
+    dm = oracle.metric_distances(q, x, "manhattan", mu, sigma)[0]
+    assert np.array_equal(de, [2.0, 0.0, np.sqrt(8.0), 2.0])
+    assert np.array_equal(dm, [2.0, 0.0, 4.0, 2.0])
+    for m in ("euclidean", "manhattan"):
+        idx, d = oracle.knn_metric(x, q, 4, m)
+        # row 0 and row 3 tie at 2: the lower index first
+        assert list(idx[0]) == [1, 0, 3, 2]
+        assert d[0, 0] == 0.0
+
+
+def test_metric_against_scipy():
+    """scipy's z-score (population deviation) and cdist, an independent
+    implementation, agree with the oracle to rounding."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    from scipy.spatial.distance import cdist
+    x = fsgen.db_rows(5, 300, 24).astype(np.float64)
+    q = fsgen.query_rows(5, 20, 24).astype(np.float64)
+    mu, sigma = oracle.standardize_stats(x)
+    zs = scipy_stats.zscore(x, axis=0, ddof=0)
+    assert np.allclose(oracle.standardize(x, mu, sigma), np.nan_to_num(zs), rtol=1e-12, atol=1e-12)
+    zq = oracle.standardize(q, mu, sigma)
+    zx = oracle.standardize(x, mu, sigma)
+    for m, sm in (("euclidean", "euclidean"), ("manhattan", "cityblock")):
+        d = oracle.metric_distances(q, x, m, mu, sigma)
+        assert np.allclose(d, cdist(zq, zx, sm), rtol=1e-12, atol=1e-12)
+
+
+def test_metric_brute_force_loop_bit_exact():
+    """The vectorised distances equal a plain loop in the stated order."""
+    import math
+    x = fsgen.db_rows(6, 12, 7).astype(np.float64)
+    q = fsgen.query_rows(6, 3, 7).astype(np.float64)
+    n, f = x.shape
+    mu = [0.0] * f
+    sg = [0.0] * f
+    for j in range(f):
+        acc = 0.0
+        for i in range(n):
+            acc = acc + x[i, j]
+        mu[j] = acc / n
+        acc = 0.0
+        for i in range(n):
+            d = x[i, j] - mu[j]
+            acc = acc + d * d
+        sg[j] = math.sqrt(acc / n)
+    m2, s2 = oracle.standardize_stats(x)
+    assert list(m2) == mu and list(s2) == sg
+    z = lambda v, j: (v - mu[j]) / sg[j] if sg[j] > 0 else 0.0  # noqa: E731
+    for metric in ("euclidean", "manhattan"):
+        d = oracle.metric_distances(q, x, metric, m2, s2)
+        for a in range(q.shape[0]):
+            for b in range(n):
+                acc = 0.0
+                for j in range(f):
+                    t = z(q[a, j], j) - z(x[b, j], j)
+                    acc = acc + (t * t if metric == "euclidean" else abs(t))
+                ref = math.sqrt(acc) if metric == "euclidean" else acc
+                assert d[a, b] == ref
+
+
+def test_metric_invariants():
+    """Standardisation makes the ranking independent of each column's scale
+    and offset; a constant column contributes nothing; permuting the rows
+    permutes the result; the k = 1 answer opens the k = 3 answer."""
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(400, 9))
+    q = rng.normal(size=(15, 9))
+    for m in ("euclidean", "manhattan"):
+        i0, d0 = oracle.knn_metric(x, q, 3, m)
+        scale = rng.uniform(0.5, 4.0, size=9)
+        shift = rng.normal(size=9)
+        i1, d1 = oracle.knn_metric(x * scale + shift, q * scale + shift, 3, m)
+        assert np.array_equal(i0, i1) and np.allclose(d0, d1, rtol=1e-9)
+        xc = np.concatenate([x, np.full((400, 1), 7.0)], axis=1)
+        qc = np.concatenate([q, np.full((15, 1), -3.0)], axis=1)
+        i2, d2 = oracle.knn_metric(xc, qc, 3, m)
+        assert np.array_equal(i0, i2) and np.array_equal(d0, d2)
+        perm = rng.permutation(400)
+        i3, _ = oracle.knn_metric(x[perm], q, 3, m)
+        assert np.array_equal(perm[i3], i0)
+        i4, _ = oracle.knn_metric(x, q, 1, m)
+        assert np.array_equal(i4[:, 0], i0[:, 0])
+        # leave-one-out: a database row as its own query, excluded
+        i5, _ = oracle.knn_metric(x, x[:10], 1, m, exclude=np.arange(10))
+        assert np.all(i5[:, 0] != np.arange(10))
+
+
+def test_metric_planted_mistake_is_caught():
+    """A plausible slip, the sample deviation (n - 1) instead of the
+    population one, changes the distances the grid pins."""
+    x = np.array([[0, 0], [2, 0], [0, 2], [2, 2]], dtype=np.float64)
+    mu, sigma = oracle.standardize_stats(x)
+    wrong = sigma * np.sqrt(4 / 3)
+    q = np.array([[2.0, 0.0]])
+    assert not np.array_equal(oracle.metric_distances(q, x, "euclidean", mu, wrong)[0],
+                              [2.0, 0.0, np.sqrt(8.0), 2.0])
