@@ -206,6 +206,26 @@ fs_status fs_db_check(fs_db *db, void *stream);
 fs_status fs_db_stats(fs_db *db, void *stream, int32_t reset, fs_stats *out);
 
 /*
+ * fs_db_set_metric - the similarity measure of later searches on db.
+ *   FS_COSINE (the default): Sec. 4.2's cosine distance, d = 1 - s.
+ *   FS_EUCLIDEAN, FS_MANHATTAN: Sec. 4.2 leaves other metrics to future
+ *   work; these are the distances between feature vectors standardised per
+ *   feature, z = (v - mu) / sigma, with the mean and population deviation
+ *   of the segment's rows (binary64, sums in row order; a feature constant
+ *   over the segment contributes nothing). d is the Euclidean or Manhattan
+ *   distance of the z vectors (binary64 for the reported rows); ranking is
+ *   d ascending, equal d to the lower index. Queries are standardised with
+ *   the statistics of their segment.
+ * Needs an FS_FP32 database (FS_EUNSUPPORTED otherwise: the tensor-core
+ * scans hold unit-vector codes). Computes the statistics and the
+ * standardised rows on `stream` and synchronises it. Not while searches on
+ * db are being issued from another thread.
+ */
+typedef enum { FS_COSINE = 0, FS_EUCLIDEAN = 1, FS_MANHATTAN = 2 } fs_metric;
+
+fs_status fs_db_set_metric(fs_db *db, fs_metric metric, void *stream);
+
+/*
  * Scan planning parameters of one database. The paper has no counterpart:
  * these only change how the scan's work is split across blocks and how
  * long its internal candidate lists are, never a result (the selection is

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfs.so")
 
 FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EUNSUPPORTED = range(6)
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp8_e4m3": 2}
+METRICS = {"cosine": 0, "euclidean": 1, "manhattan": 2}
 FS_MAX_K = 16
 FS_NOALLOC_SCRATCH_BYTES = 32 << 20
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA",
@@ -68,6 +69,7 @@ _SIGNATURES = {
     "fs_db_check": [P, P],
     "fs_db_stats": [P, P, I32, ctypes.POINTER(_Stats)],
     "fs_db_set_tuning": [P, ctypes.POINTER(_Tuning)],
+    "fs_db_set_metric": [P, ctypes.c_int, P],
     "fs_db_get_tuning": [P, ctypes.POINTER(_Tuning)],
     "fs_profile_enable": [I32],
     "fs_profile_read": [I32, ctypes.POINTER(_Profile)],
@@ -167,6 +169,7 @@ class Database:
     def __init__(self, handle, n, f, n_seg, prec, device):
         self.handle = handle
         self.n, self.f, self.n_seg, self.prec, self.device = n, f, n_seg, prec, device
+        self.metric = "cosine"
 
     def close(self):
         if self.handle:
@@ -291,6 +294,13 @@ def fs_db_stats(db: Database, reset: bool = False, stream=None) -> dict:
     st = _Stats()
     _check(lib().fs_db_stats(db.handle, _stream(stream), 1 if reset else 0, ctypes.byref(st)))
     return {n: int(getattr(st, n)) for n in STAT_FIELDS}
+
+
+def fs_db_set_metric(db: Database, metric: str = "cosine", stream=None):
+    """The similarity of later searches: "cosine" (Sec. 4.2), or "euclidean" /
+    "manhattan" on features standardised per segment (FP32 databases)."""
+    _check(lib().fs_db_set_metric(db.handle, METRICS[metric], _stream(stream)))
+    db.metric = metric
 
 
 def fs_db_set_tuning(db: Database, tuning: dict | None):

@@ -46,6 +46,13 @@ struct fs_db {
     CUtensorMap map_x;              // TMA map of the codes (tensor-core scans)
     CUtensorMap map_x_half;         // the same with half-tile boxes (pairs of CTAs)
     fs_tuning tune = {0, 0, 0, 0};  // scan planning parameters (0 = default)
+    int metric = FS_COSINE;         // fs_metric of the searches
+    double* mu = nullptr;           // [n_seg][f] standardisation statistics
+    double* sg = nullptr;
+    float* row_term = nullptr;      // [n] Euclidean 1/2 |z|^2
+    float* row_mag = nullptr;       // [n] |z| or sum |z_i|
+    float* mag_max_dev = nullptr;   // [n_seg]
+    std::vector<float> mag_max;     // host copy
 };
 
 namespace {
@@ -71,8 +78,10 @@ fs_status fail(fs_status st, const char* fmt, ...) {
 
 void free_db(fs_db* db) {
     if (!db) return;
-    void* ptrs[] = {db->raw, db->unit, db->b64, db->lowp, db->scale, db->resid, db->seq_off,
-                    db->seq_ids, db->seg_off_dev, db->r_max_dev, db->status, db->stats};
+    void* ptrs[] = {db->raw,      db->unit,      db->b64,       db->lowp,     db->scale,
+                    db->resid,    db->seq_off,   db->seq_ids,   db->seg_off_dev,
+                    db->r_max_dev, db->status,   db->stats,     db->mu,       db->sg,
+                    db->row_term, db->row_mag,   db->mag_max_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete db;
@@ -256,6 +265,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         SegPlan& p = pl.seg[s];
         std::memset(&p, 0, sizeof(p));
         p.row0 = db->seg_off[s];
+        p.seg = s;
         p.nrows = db->seg_off[s + 1] - db->seg_off[s];
         p.q0 = q_seg_off ? q_seg_off[s] : 0;
         p.nq = q_seg_off ? q_seg_off[s + 1] - q_seg_off[s] : nq;
@@ -318,10 +328,18 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.chunk_rows = (int32_t)(chunk_tiles * pl.tile_rows);
         p.chunks = p.nrows > 0 ? (int32_t)ceil_div(p.nrows, p.chunk_rows) : 0;
         p.list_t = pl.list_t;
-        const Bounds b = score_bounds(db, db->r_max[s]);
-        p.bound_scan = (float)b.scan;
-        p.bound_rq = (float)b.rq;
-        p.bound_rerank = (float)b.rerank;
+        if (is_std_metric(db->metric)) {
+            // the per-query bound is computed with the query (E = q_resid)
+            p.bound_scan = 0.0f;
+            p.bound_rq = 1.0f;
+            p.bound_rerank = 0.0f;
+            p.mag_max = db->mag_max[s];
+        } else {
+            const Bounds b = score_bounds(db, db->r_max[s]);
+            p.bound_scan = (float)b.scan;
+            p.bound_rq = (float)b.rq;
+            p.bound_rerank = (float)b.rerank;
+        }
         if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.units * row_tiles;
     }
     // number the scan items largest segment first: blocks take items round
@@ -399,6 +417,10 @@ DbView db_view(const fs_db* db) {
     v.fu = db->fu;
     v.fl = db->fl;
     v.prec = (int32_t)db->prec;
+    v.metric = db->metric;
+    v.mu = db->mu;
+    v.sg = db->sg;
+    v.row_term = db->row_term;
     return v;
 }
 
@@ -471,8 +493,11 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
         FS_CUDA(launch_write_plan(pl.seg.data(), pl.q_order.data(), db->n_seg,
                                   (SegPlan*)(ws + L.plan), (int32_t*)(ws + L.q_order), c.fb_count,
                                   c.work_counter, cs));
-        FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_ss, c.q_lowp, db->fl,
-                                    c.q_scale, c.q_resid, db->prec, db->status, cs));
+        if (is_std_metric(db->metric))
+            FS_CUDA(launch_std_queries(v, c, cs));
+        else
+            FS_CUDA(launch_prepare_rows(q, nq, db->f, c.q_unit, db->fu, c.q_ss, c.q_lowp,
+                                        db->fl, c.q_scale, c.q_resid, db->prec, db->status, cs));
         // 0 sorts below every order-mapped score
         FS_CUDA(cudaMemsetAsync(c.shared_thr, 0, sizeof(uint32_t) * nq, cs));
         t.finish((int)ceil_div(db->n_seg, 256) + 1);
@@ -680,6 +705,46 @@ fs_status fs_build_db(const float* x, int64_t n, int32_t f, const int64_t* seq_o
 #undef FS_TRY
 #undef FS_TRY_CUDA
     *out = db;
+    return FS_OK;
+}
+
+fs_status fs_db_set_metric(fs_db* db, fs_metric metric, void* stream) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    if (metric != FS_COSINE && metric != FS_EUCLIDEAN && metric != FS_MANHATTAN)
+        return fail(FS_EINVAL, "metric %d is not a fs_metric", (int)metric);
+    fs_status st = check_device(db);
+    if (st != FS_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (metric == FS_COSINE) {
+        if (db->metric != FS_COSINE)   // the unit vectors again
+            FS_CUDA(launch_prepare_rows(db->raw, db->n, db->f, db->unit, db->fu, nullptr,
+                                        db->lowp, db->fl, db->scale, db->resid, db->prec,
+                                        db->status, cs));
+        FS_CUDA(cudaStreamSynchronize(cs));
+        db->metric = FS_COSINE;
+        return FS_OK;
+    }
+    if (db->prec != FS_FP32)
+        return fail(FS_EUNSUPPORTED, "the standardised metrics need an FS_FP32 database");
+    const size_t stats = (size_t)db->n_seg * db->f;
+    if (!db->mu) {
+        st = alloc((void**)&db->mu, sizeof(double) * stats, "feature means");
+        if (st == FS_OK) st = alloc((void**)&db->sg, sizeof(double) * stats, "feature deviations");
+        if (st == FS_OK) st = alloc((void**)&db->row_term, sizeof(float) * db->n, "row terms");
+        if (st == FS_OK) st = alloc((void**)&db->row_mag, sizeof(float) * db->n, "row magnitudes");
+        if (st == FS_OK)
+            st = alloc((void**)&db->mag_max_dev, sizeof(float) * db->n_seg, "segment magnitudes");
+        if (st != FS_OK) return st;
+    }
+    FS_CUDA(launch_seg_stats(db->raw, db->seg_off_dev, db->n_seg, db->f, db->mu, db->sg, cs));
+    FS_CUDA(launch_std_rows(db->raw, db->n, db->f, db->fu, db->seg_off_dev, db->n_seg, db->mu,
+                            db->sg, (int)metric, db->unit, db->row_term, db->row_mag, cs));
+    FS_CUDA(launch_segment_max(db->row_mag, db->seg_off_dev, db->n_seg, db->mag_max_dev, cs));
+    db->mag_max.assign(db->n_seg, 0.0f);
+    FS_CUDA(cudaMemcpyAsync(db->mag_max.data(), db->mag_max_dev, sizeof(float) * db->n_seg,
+                            cudaMemcpyDeviceToHost, cs));
+    FS_CUDA(cudaStreamSynchronize(cs));
+    db->metric = metric;
     return FS_OK;
 }
 

@@ -142,8 +142,11 @@ struct SegPlan {
     float bound_rq;      //   + bound_rq * (query residual norm), per query
     float bound_rerank;  // same bound for the FP32 rescoring of the window
     int32_t units;       // scan units per row chunk: query tiles, or pairs of them
+    int32_t seg;         // index of the segment in the database
+    float mag_max;       // standardised metrics: the segment's largest row magnitude
+                         // (Euclidean |z|, Manhattan sum |z_i|), for the score bound
 };
-static_assert(sizeof(SegPlan) == 80, "SegPlan layout");
+static_assert(sizeof(SegPlan) == 88, "SegPlan layout");
 
 // Read-only device view of a database and of one call's workspace.
 struct DbView {
@@ -160,6 +163,11 @@ struct DbView {
     int64_t n;
     int32_t f, fu, fl;
     int32_t prec;
+    int32_t metric;          // fs_metric; for the standardised metrics `unit` holds the
+                             // standardised rows z (FP32), zero padded
+    const double* mu;        // [n_seg][f] per-segment feature means (standardised metrics)
+    const double* sg;        // [n_seg][f] per-segment population deviations
+    const float* row_term;   // [n] Euclidean: 1/2 |z_x|^2 (FP32 of the binary64 value)
 };
 
 struct CallView {
@@ -227,6 +235,15 @@ constexpr int kFp32Lists = 2;
 cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid,
                              cudaStream_t st);
 int scan_fp32_ctas_per_sm();
+
+// metric.cu (standardised Euclidean and Manhattan distances)
+cudaError_t launch_seg_stats(const float* raw, const int64_t* seg_off_dev, int n_seg, int f,
+                             double* mu, double* sg, cudaStream_t st);
+cudaError_t launch_std_rows(const float* raw, int64_t n, int f, int fu, const int64_t* seg_off,
+                            int n_seg, const double* mu, const double* sg, int metric,
+                            float* z, float* row_term, float* row_mag, cudaStream_t st);
+cudaError_t launch_std_queries(const DbView& db, const CallView& call, cudaStream_t st);
+__host__ __device__ constexpr bool is_std_metric(int metric) { return metric != FS_COSINE; }
 
 // scan_tc.cu (tcgen05 scan of BF16 / FP8 codes)
 constexpr int kTcTileRows = 256;

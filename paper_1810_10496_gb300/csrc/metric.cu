@@ -1,0 +1,181 @@
+// Standardised Euclidean and Manhattan distances (Sec. 4.2 leaves metrics
+// other than the cosine distance to future work; these are the library's
+// readings of the two it names for that).
+//
+// Per segment and feature, the mean and the population deviation of the
+// rows, in binary64 with sums in row order (no fused multiply-add), exactly
+// as the oracle computes them. Rows and queries are standardised to
+// z = (v - mu) / sigma (0 for a feature with sigma = 0) and stored in FP32 for
+// the FP32 scan, which scores
+//   Euclidean:  z_q . z_x - |z_x|^2 / 2   (larger is nearer: |z_q - z_x|^2 is
+//               |z_q|^2 minus twice this)
+//   Manhattan:  -sum_i |z_q,i - z_x,i|
+// Each query carries a rigorous bound E on its FP32 scores (written where the
+// cosine path keeps the code residual), so the same certified candidate
+// lists apply; the rows that reach the answer are then scored with the
+// binary64 formulas of the oracle.
+#include "fs_internal.cuh"
+
+namespace fsk {
+
+namespace {
+
+constexpr double kU = 5.9604644775390625e-08;   // 2^-24, FP32 unit roundoff
+
+// one thread per (segment, feature); consecutive features in a warp read
+// consecutive addresses of each row
+__global__ void k_seg_stats(const float* __restrict__ raw, const int64_t* __restrict__ seg_off,
+                            int n_seg, int f, double* __restrict__ mu, double* __restrict__ sg) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_seg * f) return;
+    const int s = (int)(t / f), j = (int)(t % f);
+    const int64_t lo = seg_off[s], hi = seg_off[s + 1];
+    double m = 0.0, v = 0.0;
+    if (hi > lo) {
+        const double n = (double)(hi - lo);
+        double acc = 0.0;
+        for (int64_t r = lo; r < hi; ++r) acc = __dadd_rn(acc, (double)raw[r * f + j]);
+        m = __ddiv_rn(acc, n);
+        acc = 0.0;
+        for (int64_t r = lo; r < hi; ++r) {
+            const double d = __dsub_rn((double)raw[r * f + j], m);
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        }
+        v = __dsqrt_rn(__ddiv_rn(acc, n));
+    }
+    mu[t] = m;
+    sg[t] = v;
+}
+
+__device__ __forceinline__ double zscore(float v, double m, double s) {
+    return s > 0.0 ? __ddiv_rn(__dsub_rn((double)v, m), s) : 0.0;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// one warp per row: z in FP32, the Euclidean row term, the row's magnitude
+__global__ void k_std_rows(const float* __restrict__ raw, int64_t n, int f, int fu,
+                           const int64_t* __restrict__ seg_off, int n_seg,
+                           const double* __restrict__ mu, const double* __restrict__ sg,
+                           int metric, float* __restrict__ z, float* __restrict__ row_term,
+                           float* __restrict__ row_mag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= row) lo = mid; else hi = mid - 1;
+    }
+    const double* m = mu + (int64_t)lo * f;
+    const double* s = sg + (int64_t)lo * f;
+    double sq = 0.0, sq32 = 0.0, l1 = 0.0;
+    for (int i = lane; i < fu; i += 32) {
+        const double zi = i < f ? zscore(raw[row * f + i], m[i], s[i]) : 0.0;
+        const float z32 = (float)zi;
+        z[row * fu + i] = z32;
+        sq += zi * zi;
+        sq32 += (double)z32 * (double)z32;
+        l1 += fabs((double)z32);
+    }
+    sq = warp_sum_d(sq);
+    sq32 = warp_sum_d(sq32);
+    l1 = warp_sum_d(l1);
+    if (lane == 0) {
+        row_term[row] = metric == FS_EUCLIDEAN ? (float)(0.5 * sq) : 0.0f;
+        // magnitudes rounded up (they only enter error bounds)
+        const double mag = metric == FS_EUCLIDEAN ? sqrt(sq32) : l1;
+        row_mag[row] = (float)(mag * (1.0 + 1e-6));
+    }
+}
+
+__device__ __forceinline__ int plan_index(const CallView& call, int q) {
+    int lo = 0, hi = call.n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (call.plan[call.q_order[mid]].q0 <= q) lo = mid; else hi = mid - 1;
+    }
+    return call.q_order[lo];
+}
+
+// Per call: one warp per query. z in FP32 (q_unit), a nonzero q_ss (the zero
+// vector convention is the cosine's alone) and the query's score bound E in
+// q_resid (the plan's bound_scan = 0, bound_rq = 1 make E = q_resid):
+//   Euclidean: E = 1.01 (g Q R + 3u (R^2/2 + Q R)),  Manhattan:
+//   E = 1.01 (g + 2u)(Q1 + R1), with g = gamma_(fu+2), Q / Q1 the query's
+//   |z| / sum |z_i| and R / R1 the segment's largest row magnitude. These
+//   cover the FP32 accumulation of the scan (sequential, fu terms), the
+//   rounding of z to FP32 on both sides, the rounding of the row term and of
+//   the final subtraction.
+__global__ void k_std_queries(DbView db, CallView call) {
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= call.nq) return;
+    const SegPlan p = call.plan[plan_index(call, q)];
+    const double* m = db.mu + (int64_t)p.seg * db.f;
+    const double* s = db.sg + (int64_t)p.seg * db.f;
+    const float* v = call.q_raw + (int64_t)q * db.f;
+    float* zq = call.q_unit + (int64_t)q * db.fu;
+    double sq32 = 0.0, l1 = 0.0;
+    bool ok = true;
+    for (int i = lane; i < db.fu; i += 32) {
+        float z32 = 0.0f;
+        if (i < db.f) {
+            const float vi = v[i];
+            ok &= isfinite(vi);
+            z32 = isfinite(vi) ? (float)zscore(vi, m[i], s[i]) : 0.0f;
+        }
+        zq[i] = z32;
+        sq32 += (double)z32 * (double)z32;
+        l1 += fabs((double)z32);
+    }
+    sq32 = warp_sum_d(sq32);
+    l1 = warp_sum_d(l1);
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+        if (!ok) atomicOr(db.status, kStBadFeature);
+        const double n = (double)(db.fu + 2);
+        const double g = n * kU / (1.0 - n * kU);
+        const double R = (double)p.mag_max;
+        double e;
+        if (db.metric == FS_EUCLIDEAN) {
+            const double Q = sqrt(sq32) * (1.0 + 1e-6);
+            e = 1.01 * (g * Q * R + 3.0 * kU * (0.5 * R * R + Q * R));
+        } else {
+            e = 1.01 * (g + 2.0 * kU) * (l1 * (1.0 + 1e-6) + R);
+        }
+        call.q_resid[q] = (float)(e * (1.0 + 1e-6)) + 1e-30f;
+        call.q_ss[q] = 1.0f;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_seg_stats(const float* raw, const int64_t* seg_off_dev, int n_seg, int f,
+                             double* mu, double* sg, cudaStream_t st) {
+    const int64_t t = (int64_t)n_seg * f;
+    if (t == 0) return cudaSuccess;
+    k_seg_stats<<<(unsigned)ceil_div(t, 128), 128, 0, st>>>(raw, seg_off_dev, n_seg, f, mu, sg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_std_rows(const float* raw, int64_t n, int f, int fu, const int64_t* seg_off,
+                            int n_seg, const double* mu, const double* sg, int metric,
+                            float* z, float* row_term, float* row_mag, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_std_rows<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(raw, n, f, fu, seg_off, n_seg, mu, sg,
+                                                         metric, z, row_term, row_mag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_std_queries(const DbView& db, const CallView& call, cudaStream_t st) {
+    if (call.nq == 0) return cudaSuccess;
+    k_std_queries<<<(unsigned)ceil_div(call.nq, 8), 256, 0, st>>>(db, call);
+    return cudaGetLastError();
+}
+
+}  // namespace fsk

@@ -41,6 +41,10 @@ __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t
     return lo;
 }
 
+// METRIC: FS_COSINE and FS_EUCLIDEAN accumulate dot products (Euclidean then
+// subtracts the row term 1/2 |z_x|^2), FS_MANHATTAN accumulates |a - b| and
+// scores its negation; larger is nearer in every case.
+template <int METRIC>
 __global__ void __launch_bounds__(THREADS)
 k_scan_fp32(DbView db, CallView call) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -133,18 +137,30 @@ k_scan_fp32(DbView db, CallView call) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                        for (int j = 0; j < 8; ++j) {
+                            if (METRIC == FS_MANHATTAN)
+                                acc[i][j] += fabsf(a[i] - b[j]);
+                            else
+                                acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                        }
                 }
                 buf ^= 1;
             }
             __syncthreads();  // every thread is done with the previous score tile
+            float rt[8];   // Euclidean: the rows' terms (0 past the chunk)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+                rt[j] = (METRIC == FS_EUCLIDEAN && tr + rj < row_end) ? db.row_term[tr + rj] : 0.0f;
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-                    sm.s[qi][rj] = acc[i][j];
+                    sm.s[qi][rj] = METRIC == FS_MANHATTAN ? -acc[i][j]
+                                   : (METRIC == FS_EUCLIDEAN ? acc[i][j] - rt[j] : acc[i][j]);
                 }
             }
             __syncthreads();
@@ -238,10 +254,14 @@ k_scan_fp32(DbView db, CallView call) {
 int scan_fp32_ctas_per_sm() {
     static int cached = -1;
     if (cached < 0) {
-        cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_scan_fp32<FS_COSINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(Smem));
+        cudaFuncSetAttribute(k_scan_fp32<FS_EUCLIDEAN>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaFuncSetAttribute(k_scan_fp32<FS_MANHATTAN>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_fp32, THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_fp32<FS_COSINE>, THREADS,
                                                           sizeof(Smem)) != cudaSuccess || nb < 1)
             nb = 1;
         cached = nb;
@@ -252,7 +272,12 @@ int scan_fp32_ctas_per_sm() {
 cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid, cudaStream_t st) {
     if (call.total_items == 0) return cudaSuccess;
     scan_fp32_ctas_per_sm();  // sets the shared-memory attribute once
-    k_scan_fp32<<<grid, THREADS, sizeof(Smem), st>>>(db, call);
+    if (db.metric == FS_EUCLIDEAN)
+        k_scan_fp32<FS_EUCLIDEAN><<<grid, THREADS, sizeof(Smem), st>>>(db, call);
+    else if (db.metric == FS_MANHATTAN)
+        k_scan_fp32<FS_MANHATTAN><<<grid, THREADS, sizeof(Smem), st>>>(db, call);
+    else
+        k_scan_fp32<FS_COSINE><<<grid, THREADS, sizeof(Smem), st>>>(db, call);
     return cudaGetLastError();
 }
 

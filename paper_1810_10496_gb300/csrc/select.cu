@@ -110,6 +110,24 @@ __device__ double exact_cosine(const float* __restrict__ q, const float* __restr
     return s + 0.0;  // -0 becomes +0
 }
 
+// Standardised metrics: the binary64 distance of the oracle, z = (v - mu) /
+// sigma (0 where sigma = 0) for both vectors, then the sequential sum of
+// squares (Euclidean, then the square root) or of magnitudes (Manhattan),
+// every operation rounded to nearest, no fused multiply-add.
+__device__ double exact_std_distance(const DbView& db, const SegPlan& p,
+                                     const float* __restrict__ q, const float* __restrict__ x) {
+    const double* m = db.mu + (int64_t)p.seg * db.f;
+    const double* s = db.sg + (int64_t)p.seg * db.f;
+    double acc = 0.0;
+    for (int i = 0; i < db.f; ++i) {
+        const double zq = s[i] > 0.0 ? __ddiv_rn(__dsub_rn((double)q[i], m[i]), s[i]) : 0.0;
+        const double zx = s[i] > 0.0 ? __ddiv_rn(__dsub_rn((double)x[i], m[i]), s[i]) : 0.0;
+        const double t = __dsub_rn(zq, zx);
+        acc = db.metric == FS_EUCLIDEAN ? __dadd_rn(acc, __dmul_rn(t, t)) : __dadd_rn(acc, fabs(t));
+    }
+    return db.metric == FS_EUCLIDEAN ? __dsqrt_rn(acc) : acc;
+}
+
 __device__ __forceinline__ void write_padding(const CallView& call, int q, int from) {
     for (int c = from + (threadIdx.x & 31); c < call.k_max; c += 32) {
         call.out_idx[(int64_t)q * call.k_max + c] = -1;
@@ -225,6 +243,35 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     }
     __syncwarp();
     if (!certified) return -1;
+
+    if (is_std_metric(db.metric)) {
+        // standardised metrics: every window row scored with the binary64
+        // formula (a lane each), ranked by (distance, row); the certificate
+        // holds in real arithmetic with the margin of E's 1 % inflation, far
+        // above binary64 rounding
+        const float* qr = call.q_raw + (int64_t)q * db.f;
+        for (int w = lane; w < nw; w += 32) {
+            const int64_t row = p.row0 + sh.widx[wid][w];
+            sh.s64[wid][w] = -exact_std_distance(db, p, qr, db.raw + row * (int64_t)db.f);
+        }
+        __syncwarp();
+        for (int w = lane; w < nw; w += 32) {
+            const double sw = sh.s64[wid][w];
+            const int rw = sh.widx[wid][w];
+            int rank = 0;
+            for (int v = 0; v < nw; ++v) {
+                const double sv = sh.s64[wid][v];
+                rank += (sv > sw) || (sv == sw && sh.widx[wid][v] < rw);
+            }
+            if (rank < k) {
+                call.out_idx[out0 + rank] = rw;
+                call.out_dist[out0 + rank] = (float)(-sw);
+            }
+        }
+        if (lane == 0) atomicAdd(&stats[kStatFp64], (unsigned long long)nw);
+        __syncwarp();
+        return nw < k ? nw : k;
+    }
 
     // 4. FP32 rescoring of the window: the cosine of the unit vectors and
     //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
@@ -366,7 +413,7 @@ k_select(DbView db, CallView call) {
 
         if (nrows == 0) {
             nout = 0;
-        } else if (call.q_ss[q] == 0.0f) {
+        } else if (db.metric == FS_COSINE && call.q_ss[q] == 0.0f) {
             // zero query: every cosine is 0, so the lowest indices win (d = 1)
             int c = 0;
             for (int r = 0; r < nrows && c < k; ++r) {
@@ -384,10 +431,16 @@ k_select(DbView db, CallView call) {
             const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
             nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, nl, p.list_t, E, sh.stats);
             if (nout < 0 && lane == 0) {
-                // the FP32 rescan of the fallback answers it
-                const int slot = atomicAdd(call.fb_count, 1);
-                call.fb_list[slot] = q;
-                call.q_a64[q] = exact_norm2(call.q_raw + (int64_t)q * db.f, db.f);
+                if (is_std_metric(db.metric)) {
+                    // the binary64 scan answers it directly
+                    const int slot = atomicAdd(call.fb2_count, 1);
+                    call.fb2_list[slot] = q;
+                } else {
+                    // the FP32 rescan of the fallback answers it
+                    const int slot = atomicAdd(call.fb_count, 1);
+                    call.fb_list[slot] = q;
+                    call.q_a64[q] = exact_norm2(call.q_raw + (int64_t)q * db.f, db.f);
+                }
             }
         }
         if (nout >= 0) {
@@ -542,7 +595,9 @@ k_fallback_scan(DbView db, CallView call) {
         for (int64_t r = lo + threadIdx.x; r < hi; r += kFbThreads) {
             if ((int)r == excl) continue;
             const int64_t row = p.row0 + r;
-            const double s = exact_cosine(qr, db.raw + row * db.f, db.f, a64, db.b64[row]);
+            const double s = is_std_metric(db.metric)
+                                 ? -exact_std_distance(db, p, qr, db.raw + row * db.f)
+                                 : exact_cosine(qr, db.raw + row * db.f, db.f, a64, db.b64[row]);
             if (ti[k - 1] >= 0 && !better(s, (int)r, ts[k - 1], ti[k - 1])) continue;
             int pos = k - 1;
             while (pos > 0 && (ti[pos - 1] < 0 || better(s, (int)r, ts[pos - 1], ti[pos - 1]))) {
@@ -614,7 +669,8 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
             if (biv < 0) break;
             if (lane == 0) {
                 call.out_idx[out0 + c] = biv;
-                call.out_dist[out0 + c] = (float)(1.0 - bsv);
+                call.out_dist[out0 + c] = is_std_metric(db.metric) ? (float)(-bsv)
+                                                                   : (float)(1.0 - bsv);
             }
             ++nout;
         }
