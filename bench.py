@@ -172,7 +172,7 @@ def pair_count(w):
     return int(np.sum(np.diff(so) * np.diff(qo)))
 
 
-def oracle_sample(w, nq_sample, seed=0):
+def oracle_sample(w, nq_sample, seed=0, metric="cosine"):
     """Time the CPU oracle (as it stands) on a sample of the queries, each
     against its whole database. Returns the picked queries, the oracle's
     (idx, dist, seqs, lens) per picked query, the seconds and the pairs."""
@@ -188,7 +188,11 @@ def oracle_sample(w, nq_sample, seed=0):
         lo, hi = int(so[s]), int(so[s + 1])
         off = w.seq_off[lo:hi + 1] - w.seq_off[lo]
         ids = w.seq_ids[w.seq_off[lo]:w.seq_off[hi]]
-        res = oracle.recommend(w.x[lo:hi], w.queries[qs], int(ks[s]), off, ids, 128)
+        if metric == "cosine":
+            res = oracle.recommend(w.x[lo:hi], w.queries[qs], int(ks[s]), off, ids, 128)
+        else:
+            i_o, d_o = oracle.knn_metric(w.x[lo:hi], w.queries[qs], int(ks[s]), metric)
+            res = (i_o, d_o) + oracle.gather(i_o, off, ids, 128)
         for j, q in enumerate(qs):
             out[int(q)] = tuple(r[j] for r in res)
         pairs += len(qs) * (hi - lo)
@@ -203,7 +207,7 @@ def run_reference(args):
     w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
     times, pairs = [], 0
     for s in range(args.warmup + args.steps):
-        _, _, dt, pr = oracle_sample(w, args.ref_sample, seed=s)
+        _, _, dt, pr = oracle_sample(w, args.ref_sample, seed=s, metric=args.metric)
         if s >= args.warmup:
             times.append(dt)
             pairs += pr
@@ -401,6 +405,8 @@ def run_ours(args):
 
     def make_db(prec):
         db = fs.fs_build_db(x_d, off_d, ids_d, seg_off=seg_off, prec=prec)
+        if args.metric != "cosine":
+            fs.fs_db_set_metric(db, args.metric)
         if args.tuning:
             fs.fs_db_set_tuning(db, json.loads(args.tuning))
             tuned[prec] = {"tuning": fs.fs_db_get_tuning(db), "fixed": True}
@@ -488,7 +494,14 @@ def run_ours(args):
     scan_ms = prof["ms"]["scan"] / max(1, prof["calls"]["scan"])
     flops = 2.0 * pairs * F
     peaks, peak_src = load_peaks()
-    if prec == "fp32":
+    if prec == "fp32" and args.metric == "manhattan":
+        # |a - b| then an add: two FP32 instructions per element, so half the
+        # FMA rate; work counted as 2 flop per element like the dot products
+        roof = {"bound": "alu", "achieved": flops / (scan_ms / 1e3) / 1e12,
+                "peak": FP32_SIMT_PEAK_TFLOPS / 2, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2.07 GHz x 1 element per "
+                               "2 instructions (2 flop per element)"}
+    elif prec == "fp32":
         roof = {"bound": "alu", "achieved": flops / (scan_ms / 1e3) / 1e12,
                 "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"}
@@ -552,7 +565,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8_e4m3"}[prec] + "+f64 rescoring",
         "data": "synthetic",
-        "config": {"workload": workload_desc(w), "precision": prec,
+        "config": {"workload": workload_desc(w), "precision": prec, "metric": args.metric,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "cuda_graph": bool(use_graph),
                    "plan_tuning": tuned if tuned else "default plan",
@@ -567,7 +580,7 @@ def run_ours(args):
     # CPU oracle on a bounded sample (rank 0, one GPU only), and recall of
     # the GPU answers on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pick, ores, dt, spairs = oracle_sample(w, args.cpu_sample)
+        pick, ores, dt, spairs = oracle_sample(w, args.cpu_sample, metric=args.metric)
         step(db, ws, q_d)
         torch.cuda.synchronize()
         ig = outs["idx"].cpu().numpy()
@@ -601,6 +614,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fp32_scale", choices=sorted(fsgen.CONFIGS) + ["batching"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--metric", default="cosine", choices=["cosine", "euclidean", "manhattan"],
+                    help="similarity (euclidean / manhattan: standardised, FP32 path)")
     ap.add_argument("--n", type=int, default=None,
                     help="database rows instead of the workload's (bounded profiling cases)")
     ap.add_argument("--q", type=int, default=None, help="queries instead of the workload's")
@@ -627,6 +642,8 @@ def main():
                     help="replay each step as a captured CUDA graph (default: segmented workloads)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     args = ap.parse_args()
+    if args.metric != "cosine" and args.precision != "fp32":
+        ap.error("--metric euclidean / manhattan runs on the FP32 path: add --precision fp32")
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":

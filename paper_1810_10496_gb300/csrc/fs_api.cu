@@ -421,6 +421,7 @@ DbView db_view(const fs_db* db) {
     v.mu = db->mu;
     v.sg = db->sg;
     v.row_term = db->row_term;
+    v.row_mag = db->row_mag;
     return v;
 }
 

@@ -168,6 +168,7 @@ struct DbView {
     const double* mu;        // [n_seg][f] per-segment feature means (standardised metrics)
     const double* sg;        // [n_seg][f] per-segment population deviations
     const float* row_term;   // [n] Euclidean: 1/2 |z_x|^2 (FP32 of the binary64 value)
+    const float* row_mag;    // [n] |z_x| (Euclidean) or sum |z_x,i| (Manhattan), rounded up
 };
 
 struct CallView {

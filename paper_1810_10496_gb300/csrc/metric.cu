@@ -103,11 +103,13 @@ __device__ __forceinline__ int plan_index(const CallView& call, int q) {
 }
 
 // Per call: one warp per query. z in FP32 (q_unit), a nonzero q_ss (the zero
-// vector convention is the cosine's alone) and the query's score bound E in
-// q_resid (the plan's bound_scan = 0, bound_rq = 1 make E = q_resid):
+// vector convention is the cosine's alone), the query's magnitude cap R in
+// q_scale and its score bound E in q_resid (the plan's bound_scan = 0,
+// bound_rq = 1 make E = q_resid):
 //   Euclidean: E = 1.01 (g Q R + 3u (R^2/2 + Q R)),  Manhattan:
 //   E = 1.01 (g + 2u)(Q1 + R1), with g = gamma_(fu+2), Q / Q1 the query's
-//   |z| / sum |z_i| and R / R1 the segment's largest row magnitude. These
+//   |z| / sum |z_i| and R / R1 the smaller of the segment's largest row
+//   magnitude and the query's magnitude plus D (below). These
 //   cover the FP32 accumulation of the scan (sequential, fu terms), the
 //   rounding of z to FP32 on both sides, the rounding of the row term and of
 //   the final subtraction.
@@ -136,11 +138,42 @@ __global__ void k_std_queries(DbView db, CallView call) {
     sq32 = warp_sum_d(sq32);
     l1 = warp_sum_d(l1);
     ok = __all_sync(0xffffffffu, ok);
+    // An upper bound D on the distance to the k-th nearest row: the largest
+    // distance to k rows of the segment (any k; here the first ones the query
+    // may select). A row farther than D from the query cannot be among its k
+    // nearest, and by the triangle inequality every row within D has
+    // magnitude at most |z_q| + D (Manhattan: the L1 forms), so the score
+    // bound need only cover rows up to that magnitude; rows beyond it are
+    // out whatever their FP32 score.
+    double dmax = -1.0;
+    {
+        const int excl = (call.exclude && ok) ? call.exclude[q] : -1;
+        int taken = 0;
+        dmax = 0.0;
+        for (int64_t r = 0; r < p.nrows && taken < p.k; ++r) {
+            if ((int)r == excl) continue;
+            const float* x = db.raw + (p.row0 + r) * (int64_t)db.f;
+            double acc = 0.0;
+            for (int i = lane; i < db.f; i += 32) {
+                const double t = zscore(v[i], m[i], s[i]) - zscore(x[i], m[i], s[i]);
+                acc += db.metric == FS_EUCLIDEAN ? t * t : fabs(t);
+            }
+            acc = warp_sum_d(acc);
+            const double d = db.metric == FS_EUCLIDEAN ? sqrt(acc) : acc;
+            dmax = fmax(dmax, d);
+            ++taken;
+        }
+        if (taken < p.k) dmax = -1.0;   // fewer rows than k: no bound from them
+    }
     if (lane == 0) {
         if (!ok) atomicOr(db.status, kStBadFeature);
         const double n = (double)(db.fu + 2);
         const double g = n * kU / (1.0 - n * kU);
-        const double R = (double)p.mag_max;
+        const double qmag = db.metric == FS_EUCLIDEAN ? sqrt(sq32) : l1;
+        double R = (double)p.mag_max;
+        // slack 1e-5 > the 1e-6 rounding up of the row magnitudes plus the FP32
+        // rounding of z on both sides, so every row within D stays under the cap
+        if (dmax >= 0.0) R = fmin(R, (qmag + dmax) * (1.0 + 1e-5) + 1e-30);
         double e;
         if (db.metric == FS_EUCLIDEAN) {
             const double Q = sqrt(sq32) * (1.0 + 1e-6);
@@ -149,6 +182,9 @@ __global__ void k_std_queries(DbView db, CallView call) {
             e = 1.01 * (g + 2.0 * kU) * (l1 * (1.0 + 1e-6) + R);
         }
         call.q_resid[q] = (float)(e * (1.0 + 1e-6)) + 1e-30f;
+        // the magnitude cap for the scan (rows above it score -inf: provably
+        // out, and their FP32 scores are not covered by E)
+        call.q_scale[q] = (float)R;
         call.q_ss[q] = 1.0f;
     }
 }

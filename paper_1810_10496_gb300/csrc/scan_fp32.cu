@@ -147,11 +147,21 @@ k_scan_fp32(DbView db, CallView call) {
                 buf ^= 1;
             }
             __syncthreads();  // every thread is done with the previous score tile
-            float rt[8];   // Euclidean: the rows' terms (0 past the chunk)
+            // standardised metrics: the rows' terms and magnitudes (a row above
+            // a query's magnitude cap is provably not among its k nearest and
+            // scores -inf, since its FP32 score is outside the query's bound)
+            float rt[8], mg[8], cap[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-                rt[j] = (METRIC == FS_EUCLIDEAN && tr + rj < row_end) ? db.row_term[tr + rj] : 0.0f;
+                const bool in = METRIC != FS_COSINE && tr + rj < row_end;
+                rt[j] = (METRIC == FS_EUCLIDEAN && in) ? db.row_term[tr + rj] : 0.0f;
+                mg[j] = in ? db.row_mag[tr + rj] : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+                cap[i] = (METRIC != FS_COSINE && qi < nq_tile) ? call.q_scale[qbase + qi] : INFINITY;
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -159,8 +169,10 @@ k_scan_fp32(DbView db, CallView call) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-                    sm.s[qi][rj] = METRIC == FS_MANHATTAN ? -acc[i][j]
-                                   : (METRIC == FS_EUCLIDEAN ? acc[i][j] - rt[j] : acc[i][j]);
+                    float sc = METRIC == FS_MANHATTAN ? -acc[i][j]
+                               : (METRIC == FS_EUCLIDEAN ? acc[i][j] - rt[j] : acc[i][j]);
+                    if (METRIC != FS_COSINE && mg[j] > cap[i]) sc = -INFINITY;
+                    sm.s[qi][rj] = sc;
                 }
             }
             __syncthreads();
