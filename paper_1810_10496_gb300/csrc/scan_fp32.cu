@@ -83,7 +83,9 @@ k_scan_fp32(DbView db, CallView call) {
         // the pruning bound shared by every block scanning this query (as in
         // the tensor-core scan): the k-th best score any list holds minus 2E;
         // rows below it cannot be among the k nearest
-        const bool qv = lq < nq_tile;
+        // (a zero cosine query, q_ss = 0, ties with every row and is answered
+        // by the selection from row indices alone: it offers nothing)
+        const bool qv = lq < nq_tile && call.q_ss[qbase + lq] != 0.0f;
         uint32_t* shared_p = call.shared_thr + qbase + (qv ? lq : 0);
         const float e2 =
             qv ? 2.0f * (p.bound_scan + p.bound_rq * call.q_resid[qbase + lq]) * 1.0001f : 0.0f;

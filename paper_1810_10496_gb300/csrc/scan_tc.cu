@@ -303,7 +303,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             PAIR ? mapa_shared(smem_u32(&bars.tmem_empty[0]), 0) : smem_u32(&bars.tmem_empty[0]);
         for (int64_t item = unit0; ok && item < call.total_items; item += nunits) {
             const Item w = decode(call, item, rank, PAIR);
-            const bool qvalid = lq < w.nq_tile;
+            // A zero query scores 0 against every row, so every row would tie at
+            // its list threshold and be offered; the selection answers it from
+            // row indices alone (the lowest ones, d = 1), so it is not scanned.
+            const bool qvalid = lq < w.nq_tile && call.q_ss[w.qbase + lq] != 0.0f;
             const int excl = (call.exclude && qvalid) ? call.exclude[w.qbase + lq] : -1;
             const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
             RegList<LT> st;

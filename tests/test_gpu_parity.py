@@ -134,6 +134,30 @@ def test_padding_zero_rows_and_queries(fs, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_zero_queries_among_many(fs, prec):
+    """Zero queries spread over several query tiles and the ragged tail, some
+    with a row excluded: every cosine is 0, so the lowest usable indices win
+    at d = 1, and the queries sharing their tiles and warps keep their own
+    answers."""
+    w = fsgen.make("tiny_k3", n=20000, q=300, f=256, seed=11)
+    qy = w.queries.copy()
+    zero = [0, 31, 32, 127, 130, 255, 299]
+    qy[zero] = 0.0
+    excl = np.full(300, -1, np.int32)
+    excl[[31, 130, 299]] = [0, 2, 5]
+    excl[[1, 200]] = [4, 19999]
+    db = build_db(fs, w.x, w.seq_off, w.seq_ids, prec)
+    for ex in (None, excl):
+        idx, dist, *_ = run(fs, db, qy, 4, exclude=ex)
+        i_o, d_o, _ = oracle.knn(w.x, qy, 4, exclude=ex)
+        assert_same(idx, dist, i_o, d_o)
+        for z in zero:
+            e = -1 if ex is None else ex[z]
+            assert list(idx[z]) == [r for r in range(6) if r != e][:4]
+            assert np.all(dist[z] == 1.0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_ties_and_duplicates_take_lower_index(fs, prec):
     """Exact duplicates: equal binary64 scores, lower index first. 200 copies
     of the best row overflow every candidate list, so the exact fallback scan
