@@ -505,6 +505,19 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": flops / (scan_ms / 1e3) / 1e12,
                 "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    elif w.n_seg > 1:
+        # many small databases with at most 256 queries each: about Q_s flop
+        # per code byte, below the ridge point, so HBM bounds the scan. Its
+        # algorithmic bytes: one pass over every row's codes (and FP8 row
+        # scales) plus the query codes.
+        b = 2 if prec == "bf16" else 1
+        fl = -(-F // (64 if prec == "bf16" else 128)) * (64 if prec == "bf16" else 128)
+        scan_bytes = N * fl * b + Q * fl * b + (N * 4 if prec == "fp8" else 0)
+        roof = {"bound": "hbm", "achieved": scan_bytes / (scan_ms / 1e3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peak_src} HBM copy",
+                "algorithmic_bytes": scan_bytes,
+                "tensor_tflops": flops / (scan_ms / 1e3) / 1e12}
     else:
         pk = peaks["bf16_tflops"] * (2.0 if prec == "fp8" else 1.0)
         roof = {"bound": "tensor", "achieved": flops / (scan_ms / 1e3) / 1e12, "peak": pk,

@@ -221,7 +221,7 @@ struct Plan {
 
 struct Layout {
     size_t plan, q_order, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
-        fb2_list, cand_fb, fb_score, fb_index, shared_thr, total;
+        fb2_list, cand_fb, fb_score, fb_index, shared_thr, q_plan, total;
 };
 
 bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
@@ -396,6 +396,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.fb_score = take(sizeof(double) * (size_t)nq * kFbChunks * FS_MAX_K);
     L.fb_index = take(sizeof(int32_t) * (size_t)nq * kFbChunks * FS_MAX_K);
     L.shared_thr = take(sizeof(uint32_t) * nq);
+    L.q_plan = take(sizeof(int32_t) * nq);
     L.total = off;
     return L;
 }
@@ -480,6 +481,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.fb_score = (double*)(ws + L.fb_score);
     c.fb_index = (int32_t*)(ws + L.fb_index);
     c.shared_thr = (uint32_t*)(ws + L.shared_thr);
+    c.q_plan = (int32_t*)(ws + L.q_plan);
     c.exclude = exclude;
     c.out_idx = idx;
     c.out_dist = dist;
@@ -494,6 +496,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
         FS_CUDA(launch_write_plan(pl.seg.data(), pl.q_order.data(), db->n_seg,
                                   (SegPlan*)(ws + L.plan), (int32_t*)(ws + L.q_order), c.fb_count,
                                   c.work_counter, cs));
+        FS_CUDA(launch_query_plan(c, (int32_t*)(ws + L.q_plan), cs));
         if (is_std_metric(db->metric))
             FS_CUDA(launch_std_queries(v, c, cs));
         else
@@ -501,7 +504,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
                                         db->fl, c.q_scale, c.q_resid, db->prec, db->status, cs));
         // 0 sorts below every order-mapped score
         FS_CUDA(cudaMemsetAsync(c.shared_thr, 0, sizeof(uint32_t) * nq, cs));
-        t.finish((int)ceil_div(db->n_seg, 256) + 1);
+        t.finish((int)ceil_div(db->n_seg, 256) + 2);
     }
     if (pl.total_items > 0) {
         StageTimer t(FS_STAGE_SCAN, cs);

@@ -174,6 +174,7 @@ struct DbView {
 struct CallView {
     const SegPlan* plan;      // [n_seg], in scan-item order (largest work first)
     const int32_t* q_order;   // [n_seg] plan indices sorted by first query
+    const int32_t* q_plan;    // [nq] plan index of each query's segment
     const float* q_raw;       // [nq][f] caller's queries
     double* q_a64;            // [nq] binary64 sum of squares (queries sent to the fallback)
     float* q_ss;              // [nq] FP32 sum of squares (0 exactly for a zero query)
@@ -221,6 +222,7 @@ cudaError_t launch_segment_max(const float* v, const int64_t* seg_off_dev, int n
 cudaError_t launch_write_plan(const SegPlan* host_plan, const int32_t* host_q_order, int n_seg,
                               SegPlan* dev_plan, int32_t* dev_q_order, int32_t* fb_count,
                               int32_t* work_counter, cudaStream_t st);
+cudaError_t launch_query_plan(const CallView& call, int32_t* q_plan, cudaStream_t st);
 cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st);
 cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
                             cudaStream_t st);

@@ -93,15 +93,6 @@ __global__ void k_std_rows(const float* __restrict__ raw, int64_t n, int f, int 
     }
 }
 
-__device__ __forceinline__ int plan_index(const CallView& call, int q) {
-    int lo = 0, hi = call.n_seg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (call.plan[call.q_order[mid]].q0 <= q) lo = mid; else hi = mid - 1;
-    }
-    return call.q_order[lo];
-}
-
 // Per call: one warp per query. z in FP32 (q_unit), a nonzero q_ss (the zero
 // vector convention is the cosine's alone), the query's magnitude cap R in
 // q_scale and its score bound E in q_resid (the plan's bound_scan = 0,
@@ -117,7 +108,7 @@ __global__ void k_std_queries(DbView db, CallView call) {
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= call.nq) return;
-    const SegPlan p = call.plan[plan_index(call, q)];
+    const SegPlan p = call.plan[call.q_plan[q]];
     const double* m = db.mu + (int64_t)p.seg * db.f;
     const double* s = db.sg + (int64_t)p.seg * db.f;
     const float* v = call.q_raw + (int64_t)q * db.f;

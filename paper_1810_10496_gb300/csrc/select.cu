@@ -55,15 +55,12 @@ __global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* dst_
     }
 }
 
-// The plan entry of query q: the last entry, in first-query order, whose
-// first query is <= q (segments without queries precede the one that owns q).
-__device__ __forceinline__ int plan_of_query(const CallView& call, int q) {
-    int lo = 0, hi = call.n_seg - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (call.plan[call.q_order[mid]].q0 <= q) lo = mid; else hi = mid - 1;
-    }
-    return call.q_order[lo];
+// q_plan[q] = the plan entry of the segment that owns query q: block b
+// writes entry b's queries (segments partition the queries in order).
+__global__ void k_query_plan(const SegPlan* __restrict__ plan, int32_t* __restrict__ q_plan) {
+    const int b = blockIdx.x;
+    const int q0 = plan[b].q0, nq = plan[b].nq;
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) q_plan[q0 + i] = b;
 }
 
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
@@ -225,13 +222,15 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     //    entry by entry until no list has one left
     int nw = 0;
     if (certified && ntop > 0) {
-        const double lo = tk - 2.0 * E;
+        // a float v satisfies v >= lo exactly when v >= lo rounded up to
+        // float: the test runs in FP32 (binary64 instructions are scarce)
+        const float lo = __double2float_ru(tk - 2.0 * E);
         for (int l0 = 0; l0 < nl; l0 += 32) {
             const int l = l0 + lane;
             const uint64_t* L = cand + (int64_t)l * lt;
             for (int e = 0; e < lt; ++e) {
                 const uint64_t v = l < nl ? L[e] : 0;
-                const bool in = v != 0 && (double)key_score(v) >= lo;
+                const bool in = v != 0 && key_score(v) >= lo;
                 const unsigned m = __ballot_sync(kFull, in);
                 if (m == 0) break;
                 const int pos = nw + __popc(m & ((1u << lane) - 1));
@@ -328,14 +327,24 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     // 6. near-tie clusters reaching into the first k places: runs whose
     //    neighbouring rescored values differ by at most 2 E_r
     int ncl = 0, nfp = 0;
-    if (lane == 0) {
+    // close[j]: window place j is within 2 E_r of place j - 1 (every lane
+    // tests one place, so the binary64 gaps cost one instruction per 32)
+    uint64_t close = 0;
+    {
         const double er2 = 2.0 * (double)p.bound_rerank;
+        for (int j0 = 0; j0 < nw; j0 += 32) {
+            const int j = j0 + lane;
+            const bool c = j > 0 && j < nw &&
+                           (double)sh.ssc[wid][j - 1] - (double)sh.ssc[wid][j] <= er2;
+            close |= (uint64_t)__ballot_sync(kFull, c) << j0;
+        }
+    }
+    if (lane == 0) {
         int pos = 0;
         const int lim = min(k, nw);
         while (pos < lim) {
             int end = pos + 1;
-            while (end < nw && (double)sh.ssc[wid][end - 1] - (double)sh.ssc[wid][end] <= er2)
-                ++end;
+            while (end < nw && ((close >> end) & 1)) ++end;
             if (end - pos >= 2) {
                 sh.cl_begin[wid][ncl] = (int16_t)pos;
                 sh.cl_end[wid][ncl] = (int16_t)end;
@@ -395,7 +404,8 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     return nout;
 }
 
-__global__ void __launch_bounds__(kSelWarps * 32)
+// (at most 48 registers: five blocks per SM, fewer waves on large batches)
+__global__ void __launch_bounds__(kSelWarps * 32, 5)
 k_select(DbView db, CallView call) {
     __shared__ SelShared sh;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -404,7 +414,7 @@ k_select(DbView db, CallView call) {
     const int q = blockIdx.x * kSelWarps + wid;
 
     if (q < call.nq) {
-        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
         const int excl = call.exclude ? call.exclude[q] : -1;
@@ -479,7 +489,7 @@ k_fb_scan32(DbView db, CallView call) {
     for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
         const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
         const int q = call.fb_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const SegPlan p = call.plan[call.q_plan[q]];
         const int excl = call.exclude ? call.exclude[q] : -1;
         const int64_t per = ceil_div(p.nrows, kFbChunks);
         const int64_t lo = p.row0 + chunk * per, hi = p.row0 + min(p.nrows, (int64_t)(chunk + 1) * per);
@@ -545,7 +555,7 @@ k_fb_select(DbView db, CallView call) {
     const int nfb = *call.fb_count;
     for (int slot = blockIdx.x * kSelWarps + wid; slot < nfb; slot += gridDim.x * kSelWarps) {
         const int q = call.fb_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const SegPlan p = call.plan[call.q_plan[q]];
         const uint64_t* cand = call.cand_fb + (int64_t)slot * kFbChunks * kListT;
         const int nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, kFbChunks, kListT,
                                            (double)p.bound_rerank, sh.stats);
@@ -580,7 +590,7 @@ k_fallback_scan(DbView db, CallView call) {
     for (int64_t it = blockIdx.x; it < (int64_t)nfb * kFbChunks; it += gridDim.x) {
         const int slot = (int)(it / kFbChunks), chunk = (int)(it % kFbChunks);
         const int q = call.fb2_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
         const int excl = call.exclude ? call.exclude[q] : -1;
         const double a64 = call.q_a64[q];
@@ -649,7 +659,7 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
     const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (slot < nfb) {
         const int q = call.fb2_list[slot];
-        const SegPlan p = call.plan[plan_of_query(call, q)];
+        const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
         // lane c < kFbChunks owns chunk c's sorted list
@@ -701,7 +711,7 @@ __global__ void k_gather(DbView db, CallView call, int16_t* __restrict__ seq_out
         ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kGatherPerWarp + grp;
     if (w >= (int64_t)call.nq * call.k_max) return;   // whole groups leave together
     const int q = (int)(w / call.k_max), c = (int)(w % call.k_max);
-    const SegPlan p = call.plan[plan_of_query(call, q)];
+    const SegPlan p = call.plan[call.q_plan[q]];
     const int r = call.out_idx[w];
     int16_t* dst = seq_out + w * l_max;
     int64_t lo = 0, len = 0;
@@ -749,6 +759,12 @@ cudaError_t launch_write_plan(const SegPlan* host_plan, const int32_t* host_q_or
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_query_plan(const CallView& call, int32_t* q_plan, cudaStream_t st) {
+    if (call.nq == 0 || call.n_seg == 0) return cudaSuccess;
+    k_query_plan<<<(unsigned)call.n_seg, 256, 0, st>>>(call.plan, q_plan);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st) {

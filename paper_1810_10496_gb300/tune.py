@@ -90,10 +90,13 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE):
     os.replace(tmp, path)
 
 
-def choose(measure, cands: list[dict], same) -> dict:
+def choose(measure, cands: list[dict], same, finalists: int = 3) -> dict:
     """Times every candidate with measure(c) -> (ms, answers), checks its
     answers against the first candidate's with same(a, b) and returns the
-    fastest with the timings of all."""
+    fastest with the timings of all. The fastest `finalists` and the
+    defaults are then timed once more, in reverse order, and each keeps its
+    better time: a first timing taken while the clocks or caches were still
+    settling does not decide the choice."""
     tried = []
     base = None
     for c in cands:
@@ -103,13 +106,21 @@ def choose(measure, cands: list[dict], same) -> dict:
         elif not same(ans, base):
             raise RuntimeError(f"tuning {c} changed the answers")
         tried.append({"tuning": dict(c), "ms": float(ms)})
+    again = sorted(range(len(tried)), key=lambda i: tried[i]["ms"])[:max(1, finalists)]
+    if 0 not in again:
+        again.append(0)
+    for i in sorted(again, reverse=True):
+        ms, ans = measure(cands[i])
+        if not same(ans, base):
+            raise RuntimeError(f"tuning {cands[i]} changed the answers")
+        tried[i]["ms"] = min(tried[i]["ms"], float(ms))
     best = min(tried, key=lambda t: t["ms"])
     return {"tuning": best["tuning"], "ms": best["ms"], "default_ms": tried[0]["ms"],
             "tried": tried}
 
 
 def autotune(db, q, k, q_seg_off=None, reps: int = 5, cache_path: str | None = DEFAULT_CACHE,
-             force: bool = False, cands: list[dict] | None = None) -> dict:
+             force: bool = False, cands: list[dict] | None = None, warm_s: float = 0.2) -> dict:
     """Picks the fastest tuning of `db` for batches shaped like (q, k,
     q_seg_off), applies it to `db` and returns {"tuning", "ms",
     "default_ms", "tried", "key", "cached"}. With a cache entry for the
@@ -161,6 +172,18 @@ def autotune(db, q, k, q_seg_off=None, reps: int = 5, cache_path: str | None = D
         d0, d1 = a[1][fin], b[1][fin]
         return bool(np.all(np.abs(d0 - d1) <= 1e-5 * np.abs(d1) + 1e-6))
 
+    # the first calls after a build or an idle spell run slow (clocks still
+    # rising, first touches of the workspace): run the defaults for a while
+    import time
+    fs.fs_db_set_tuning(db, cands[0])
+    t_end = time.perf_counter() + warm_s
+    n = 0
+    while n < 3 or time.perf_counter() < t_end:
+        fs.fs_knn(db, q, kk, q_seg_off=q_seg_off, workspace=ws, idx=idx, dist=dist)
+        n += 1
+        if n % 8 == 0:
+            torch.cuda.synchronize(q.device)
+    torch.cuda.synchronize(q.device)
     res = choose(measure, cands, same)
     fs.fs_db_set_tuning(db, res["tuning"])
     fs.fs_db_check(db)

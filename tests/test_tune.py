@@ -54,3 +54,21 @@ def test_choose_fastest_and_consistency():
     assert res["default_ms"] == 10.0 and len(res["tried"]) == len(cands)
     with pytest.raises(RuntimeError):
         tune.choose(lambda c: (1.0, tune._normal(c, "bf16", 3)), cands, lambda a, b: a == b)
+
+
+def test_choose_retimes_finalists():
+    """A candidate whose first timing was slow (measured while the GPU was
+    still settling) is timed again and wins if it is the fastest."""
+    cands = tune.candidates("bf16", 8, 3)
+    calls = {}
+
+    def measure(c):
+        key = tune._normal(c, "bf16", 3)
+        calls[key] = calls.get(key, 0) + 1
+        if key == tune._normal(cands[0], "bf16", 3):
+            return (5.0 if calls[key] == 1 else 1.0), "same"
+        return 1.2, "same"
+
+    res = tune.choose(measure, cands, lambda a, b: a == b)
+    assert res["tuning"] == cands[0] and res["ms"] == 1.0 and res["default_ms"] == 1.0
+    assert sum(calls.values()) == len(cands) + 4
