@@ -25,10 +25,13 @@
 //   * FP8 scores are acc * s_row * s_query (per-vector scales, Sec. 4.2's
 //     cosine of the dequantised vectors); BF16 scores are acc itself.
 //
-// Work items (query tile, row chunk) are taken in a fixed round-robin order,
-// so all roles know the sequence without talking to each other; items of one
-// chunk are numbered consecutively so concurrently running blocks share its
-// rows in L2. Every wait is bounded; a wait that gives up marks the launch
+// Work items (query tile, row chunk) are claimed one at a time from a global
+// counter by the TMA thread, which passes each to the MMA thread and the
+// epilogue warps through a small queue in shared memory, so blocks that
+// drew short items take more of them (items differ in size when databases
+// do). Pairs of CTAs take a fixed round-robin order instead, which both CTAs
+// of a pair know without talking. Items of one chunk are numbered
+// consecutively so concurrently running blocks share its rows in L2. Every wait is bounded; a wait that gives up marks the launch
 // failed (status word), and all roles then leave their loops, wait for their
 // own outstanding copies and MMAs (bounded), free TMEM and return.
 #include <cudaTypedefs.h>
@@ -54,6 +57,7 @@ constexpr uint32_t kABlockBytes = BM * 128; // one 128-byte K block of BM querie
 constexpr int kMaxKBlocks = 4;              // 256 BF16 or 512 FP8 features
 constexpr int kAccs = 512 / BN;              // accumulators in tensor memory
 constexpr uint32_t kTmemCols = kAccs * BN;
+constexpr int kItemQ = 4;                   // claimed items handed on, at most
 
 struct Bars {
     uint64_t full[kMaxStages];
@@ -66,7 +70,34 @@ struct Bars {
     uint64_t sx_ready[kAccs];   // FP8: the tile's row scales are staged
     uint64_t pfull[kMaxStages]; // pairs (leader): the odd CTA's ring slot landed
     uint64_t pa_full;           // pairs (leader): the odd CTA's query tile landed
+    uint64_t item_full[kItemQ]; // a claimed item (or the end, -1) is in item_q
+    uint64_t item_empty[kItemQ];// the MMA thread and every epilogue warp have read it
 };
+
+// The TMA thread claims the n-th item of this CTA and hands it on (-1: no
+// items left). False when a wait gave up.
+__device__ __forceinline__ bool claim_item(Bars& bars, volatile int32_t* item_q,
+                                           const CallView& call, uint32_t n,
+                                           volatile int* abort_flag, int64_t& item) {
+    const uint32_t slot = n % kItemQ, ph = (n / kItemQ) & 1;
+    if (!mbar_wait(smem_u32(&bars.item_empty[slot]), ph ^ 1, abort_flag)) return false;
+    int32_t v = atomicAdd(call.work_counter, 1);
+    if ((int64_t)v >= call.total_items) v = -1;
+    item_q[slot] = v;
+    mbar_arrive(smem_u32(&bars.item_full[slot]));
+    item = v;
+    return true;
+}
+
+// Another role reads the n-th item; the caller then arrives on
+// item_empty[n % kItemQ] (once per thread or warp counted there).
+__device__ __forceinline__ bool take_item(Bars& bars, const volatile int32_t* item_q, uint32_t n,
+                                          volatile int* abort_flag, int64_t& item) {
+    const uint32_t slot = n % kItemQ, ph = (n / kItemQ) & 1;
+    if (!mbar_wait(smem_u32(&bars.item_full[slot]), ph, abort_flag)) return false;
+    item = item_q[slot];
+    return true;
+}
 
 __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
     int lo = 0, hi = n_seg - 1;
@@ -124,6 +155,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     __shared__ Bars bars;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
+    __shared__ int32_t item_q[kItemQ];
     __shared__ __align__(16) float sx[kAccs][BN];   // FP8: the tile's row scales, per accumulator
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,6 +187,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         mbar_init(smem_u32(&bars.a_full), 1);
         mbar_init(smem_u32(&bars.a_empty), 1);
         mbar_init(smem_u32(&bars.drain), 1);
+        for (int i = 0; i < kItemQ; ++i) {
+            mbar_init(smem_u32(&bars.item_full[i]), 1);
+            mbar_init(smem_u32(&bars.item_empty[i]), 1 + kEpiWarps);
+        }
         for (int a = 0; a < kAccs; ++a) mbar_init(smem_u32(&bars.sx_ready[a]), kEpiThreads);
         fence_barrier_init();
     }
@@ -178,7 +214,14 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             prefetch_tensormap(&map_x);
             uint32_t it = 0, ic = 0, a_loads = 0;
             bool ok = true;
-            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
+            for (uint32_t n = 0; ok; ++n, ++ic) {
+                int64_t item = unit0 + (int64_t)n * nunits;
+                if (PAIR) {
+                    if (item >= call.total_items) break;
+                } else {
+                    ok = claim_item(bars, item_q, call, n, &abort_flag, item);
+                    if (!ok || item < 0) break;
+                }
                 const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag);
                 if (!ok) break;
@@ -219,7 +262,16 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 else
                     mma_commit(smem_u32(&bar));
             };
-            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
+            for (uint32_t n = 0; ok; ++n, ++ic) {
+                int64_t item = unit0 + (int64_t)n * nunits;
+                if (PAIR) {
+                    if (item >= call.total_items) break;
+                } else {
+                    ok = take_item(bars, item_q, n, &abort_flag, item);
+                    if (!ok) break;
+                    mbar_arrive(smem_u32(&bars.item_empty[n % kItemQ]));
+                    if (item < 0) break;
+                }
                 const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
                 if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pa_full), ic & 1, &abort_flag);
@@ -301,7 +353,18 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         // the barrier that frees an accumulator: the leader's
         const uint32_t r_tmem_empty0 =
             PAIR ? mapa_shared(smem_u32(&bars.tmem_empty[0]), 0) : smem_u32(&bars.tmem_empty[0]);
-        for (int64_t item = unit0; ok && item < call.total_items; item += nunits) {
+        for (uint32_t n = 0; ok; ++n) {
+            int64_t item = unit0 + (int64_t)n * nunits;
+            if (PAIR) {
+                if (item >= call.total_items) break;
+            } else {
+                ok = take_item(bars, item_q, n, &abort_flag, item);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars.item_empty[n % kItemQ]));
+                if (item < 0) break;
+            }
             const Item w = decode(call, item, rank, PAIR);
             // A zero query scores 0 against every row, so every row would tie at
             // its list threshold and be offered; the selection answers it from
