@@ -290,8 +290,9 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
     // chunks of a segment; those chunks should fit in half of L2 so the query
     // tiles of a chunk read its rows from L2, not HBM. (3) Among chunk counts
     // meeting (1) and (2), take the one that fills the last round of items
-    // best (blocks take items round robin). The 4 and the half are the
-    // defaults of the tuning parameters items_per_block and l2_share_pct.
+    // best (blocks take items in number order, one at a time). The 4 and the
+    // half are the defaults of the tuning parameters items_per_block and
+    // l2_share_pct.
     const int items_per_block = db->tune.items_per_block ? db->tune.items_per_block : 4;
     const int l2_pct = db->tune.l2_share_pct ? db->tune.l2_share_pct : 50;
     const int64_t desired = (int64_t)pl.slots * items_per_block;
@@ -342,8 +343,8 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         }
         if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.units * row_tiles;
     }
-    // number the scan items largest segment first: blocks take items round
-    // robin, so the long ones start first and the short ones fill in
+    // number the scan items largest segment first: blocks take items in
+    // number order, so the long ones start first and the short ones fill in
     std::vector<int32_t> order(n_seg);
     for (int s = 0; s < n_seg; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(),
