@@ -23,7 +23,7 @@ DEFAULT_CACHE = os.environ.get(
     "FS_TUNE_CACHE",
     os.path.join(os.path.expanduser("~"), ".cache", "paper_1810_10496_gb300", "tuning.json"))
 
-ITEMS_PER_BLOCK = (2, 4, 8, 16)
+ITEMS_PER_BLOCK = (1, 2, 4, 8, 16)
 LIST_LEN = (4, 8, 16)
 L2_SHARE_PCT = (25, 50, -1)
 
