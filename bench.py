@@ -288,7 +288,10 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                "offered_qps": rate, "served_qps": nq / wall,
                "clocks": sampler.summary(), "scan_ms_1024": prof["ms"]["scan"],
                "tile_batch_ms": tile_ms, "min_batch": args.min_batch,
-               "max_wait_ms": max_wait * 1e3, "held_for_fill": srv.stats.held_for_fill}
+               "max_wait_ms": max_wait * 1e3, "held_for_fill": srv.stats.held_for_fill,
+               # kernels per fs_recommend call (from the profiled call) x batches served
+               "gpu_launches": int(round(prof["launches"] / max(1, prof["calls"]["prepare"])
+                                         * srv.stats.batches))}
         res.update(serve.latency_summary(reqs))
         # sample of answers for the oracle check
         res["_sample"] = reqs[::max(1, len(reqs) // 16)][:16]
@@ -329,7 +332,7 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                 "h2d_bytes_per_step": int(r16["queries"] * w.f * 4 / r16["batches"]),
                 "d2h_bytes_per_step": int(r16["queries"] * k * (12 + 2 * 128) / r16["batches"]),
                 "note": "the serving loop is end to end: host queries in, host results out"},
-        "gpu_launches": None, "roofline": roof,
+        "gpu_launches": r16["gpu_launches"], "roofline": roof,
         "serving": {kk: v for kk, v in r16.items() if not kk.startswith("_")},
         "vs_fp32_scan": None if r32 is None else {
             "fp32_offered_qps": args.fp32_rate, "fp32_served_qps": r32["served_qps"],
