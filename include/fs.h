@@ -231,8 +231,10 @@ fs_status fs_db_set_metric(fs_db *db, fs_metric metric, void *stream);
  * long its internal candidate lists are, never a result (the selection is
  * exact whatever they are). A field left 0 takes the built-in default.
  *   items_per_block  scan work items (query tile x row chunk) per resident
- *                    block, 1..64; more items balance uneven segments better,
- *                    fewer keep longer row chunks per item (default 4).
+ *                    block, 1..64 (blocks claim items one at a time); more
+ *                    items leave finer pieces for the end of the scan, fewer
+ *                    keep longer row chunks per item, so fewer candidate
+ *                    lists start empty (default 4).
  *   list_len         entries per candidate list of the tensor-core scans:
  *                    4, 8 or 16. 4 takes effect only when every k of a call
  *                    is <= 4, 8 only when every k is <= 8; otherwise the
