@@ -8,10 +8,11 @@ candidate lists, certification, FP32 rerank and binary64 rescoring, and the
 gather of the neighbours' phase orders. The database itself is prepared once
 (fs_build_db) before timing, as a reference set is in the paper.
 
-Default workload: 1,048,576 database rows x 128 features, 4,096 queries,
-k = 3, phase orders of 1-128 pass IDs (synthetic instruction-mix vectors
-standing in for the paper's MILEPOST features). ``--impl reference`` times
-the CPU oracle instead, on a bounded sample of the same workload.
+Default workload: 16,777,216 database rows x 256 features, 8,192 queries,
+k = 3, phase orders of 1-128 pass IDs, BF16 tensor-core scan with certified
+FP32 / binary64 rerank (synthetic instruction-mix vectors standing in for the
+paper's MILEPOST features). ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
 
 Prints one JSON line (rank 0).
 """
@@ -200,18 +201,34 @@ def oracle_sample(w, nq_sample, seed=0, metric="cosine"):
     return pick, out, dt, pairs
 
 
+# The CPU oracle's cost per (query, database element), measured on the GPU
+# box's 16 host cores (1.46 s per query on 16,777,216 x 256; 53 queries/s on
+# 1,048,576 x 128): used only to size the bounded CPU samples so that a
+# default run stays within minutes.
+ORACLE_S_PER_ELEMENT = 1.0 / 2.9e9
+
+
+def oracle_sample_size(w, seconds: float, lo: int, hi: int) -> int:
+    """Queries whose oracle answers take about `seconds` on the host cores."""
+    _, so, qo, _ = segment_arrays(w)
+    per_query = float(np.sum(np.diff(so) * np.diff(qo))) / max(1, w.q) * w.f * ORACLE_S_PER_ELEMENT
+    return int(min(hi, w.q, max(lo, round(seconds / max(per_query, 1e-9)))))
+
+
 def run_reference(args):
     world, rank, _ = setup_dist()
     if rank != 0:
         return 0
     w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
+    # each step a bounded sample: about 4 s of oracle work
+    nq = args.ref_sample if args.ref_sample else oracle_sample_size(w, 4.0, 1, 32)
     times, pairs = [], 0
     for s in range(args.warmup + args.steps):
-        _, _, dt, pr = oracle_sample(w, args.ref_sample, seed=s, metric=args.metric)
+        _, _, dt, pr = oracle_sample(w, nq, seed=s, metric=args.metric)
         if s >= args.warmup:
             times.append(dt)
             pairs += pr
-    nq = min(args.ref_sample, w.q)
+    nq = min(nq, w.q)
     sec = float(np.sum(times))
     value = pairs / sec
     line = {
@@ -492,8 +509,10 @@ def run_ours(args):
         return total, per, prof, launches_per_step, (sampler.summary() if sampler else None)
 
     prec = args.precision
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     db, ws = make_db(prec)
+    torch.cuda.synchronize()    # the build's kernels are done
     build_s = time.perf_counter() - t0
     fs.fs_db_stats(db, reset=True)
     total_ms, per, prof, lps, clocks = timed(db, ws, args.steps, args.warmup,
@@ -579,8 +598,10 @@ def run_ours(args):
     vs_fp32 = None
     if prec != "fp32" and not args.no_fp32_compare:
         db32, ws32 = make_db("fp32")
-        n32 = max(3, args.steps // 4)
-        t32, per32, _, _, _ = timed(db32, ws32, n32, 2, graph=use_graph)
+        # the FP32 scan is tens of times slower: a few steps, about 30 s at most
+        slow = pairs * F > 1e14
+        n32 = 3 if slow else max(3, args.steps // 4)
+        t32, per32, _, _, _ = timed(db32, ws32, n32, 1 if slow else 2, graph=use_graph)
         v32 = pairs * n32 / (t32 / 1e3)
         vs_fp32 = {"fp32_pairs_per_s": v32, "fp32_ms_per_step": t32 / n32,
                    "speedup": (pairs * args.steps / (total_ms / 1e3)) / v32}
@@ -607,7 +628,9 @@ def run_ours(args):
     # CPU oracle on a bounded sample (rank 0, one GPU only), and recall of
     # the GPU answers on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pick, ores, dt, spairs = oracle_sample(w, args.cpu_sample, metric=args.metric)
+        # a bounded sample: about 15 s of oracle work on the host cores
+        ncpu = args.cpu_sample if args.cpu_sample else oracle_sample_size(w, 15.0, 8, 128)
+        pick, ores, dt, spairs = oracle_sample(w, ncpu, metric=args.metric)
         step(db, ws, q_d)
         torch.cuda.synchronize()
         ig = outs["idx"].cpu().numpy()
@@ -639,14 +662,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="fp32_scale", choices=sorted(fsgen.CONFIGS) + ["batching"])
+    ap.add_argument("--workload", default="precision", choices=sorted(fsgen.CONFIGS) + ["batching"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--metric", default="cosine", choices=["cosine", "euclidean", "manhattan"],
                     help="similarity (euclidean / manhattan: standardised, FP32 path)")
     ap.add_argument("--n", type=int, default=None,
                     help="database rows instead of the workload's (bounded profiling cases)")
     ap.add_argument("--q", type=int, default=None, help="queries instead of the workload's")
-    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="queries of the CPU-oracle sample (default: about 15 s of work)")
     ap.add_argument("--rate", type=float, default=500_000,
                     help="serving: offered queries per second (Poisson)")
     ap.add_argument("--fp32-rate", type=float, default=10_000,
@@ -657,7 +681,8 @@ def main():
                     help="serving: queries a batch waits for while another is in flight")
     ap.add_argument("--max-wait-ms", type=float, default=None,
                     help="serving: longest such wait (default: the time of a 128-query batch)")
-    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--ref-sample", type=int, default=None,
+                    help="--impl reference: queries per step (default: about 4 s of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,

@@ -174,12 +174,14 @@ fs_status fs_recommend(const fs_db *db, const float *q, int32_t nq,
  * fixed array of FS_NOALLOC_SCRATCH_BYTES in the library's own device memory,
  * present on every GPU the library is loaded on until the process exits.
  *   - It never allocates or frees device memory.
- *   - A call whose scratch need (fs_workspace_size for the same nq and
- *     q_seg_off) exceeds FS_NOALLOC_SCRATCH_BYTES returns FS_ENOMEM and
- *     launches nothing.
+ *   - A call whose scratch need for its own nq, q_seg_off and k (at most
+ *     what fs_workspace_size reports for the same nq and q_seg_off) exceeds
+ *     FS_NOALLOC_SCRATCH_BYTES returns FS_ENOMEM and launches nothing.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture. cudaDeviceReset unloads the library's device code, so
+ *     the address looked up before it is no longer valid: do not call this
+ *     entry point on a device after resetting it in the same process.
  *   - All calls on a device share the one array, which keeps what the last
  *     call left there; each call resets the counters it relies on and writes
  *     every other byte before reading it. Calls whose work overlaps on the
@@ -265,6 +267,26 @@ typedef struct {
 
 fs_status fs_db_set_tuning(fs_db *db, const fs_tuning *t);
 fs_status fs_db_get_tuning(const fs_db *db, fs_tuning *out);
+
+/*
+ * fs_db_set_wait_test - a test aid for the failure reporting; the paper has
+ * no counterpart. Every wait of the tensor-core scans (BF16, FP8) is bounded:
+ * a wait that runs out makes the scan's blocks stop, release what they hold
+ * and record FS_ETIMEOUT, which the next fs_db_check returns; the queries of
+ * that call then get padding (-1, +inf), never a partial answer.
+ *   withhold_first_load  nonzero: in later searches on db, every scan block
+ *                        skips the copy of its first database tile, so the
+ *                        wait for it runs out (no copy or tensor-core
+ *                        operation is left in flight; nothing faults).
+ *                        0: normal searches.
+ *   wait_limit_us        limit of every bounded wait of the scan, in
+ *                        microseconds (1..2,000,000); 0 restores the default
+ *                        of 2 s.
+ * FS_EINVAL for a limit above 2 s. Not while searches on db are being issued
+ * from another thread.
+ */
+fs_status fs_db_set_wait_test(fs_db *db, int32_t withhold_first_load,
+                              uint32_t wait_limit_us);
 
 /*
  * Stage timing (tracing). While enabled, every fs_knn / fs_recommend call

@@ -163,19 +163,22 @@ def knn(x: np.ndarray, queries: np.ndarray, k: int, chunk: int = 65536,
     of its reference set. Returns ``(idx int64[nq, k], dist float64[nq, k],
     score float64[nq, k])``; padded slots hold -1, +inf and -inf (reading 4).
     """
-    x = np.asarray(x, dtype=np.float64)
     q = np.asarray(queries, dtype=np.float64)
     nq, n = q.shape[0], x.shape[0]
     if k < 1:
         raise ValueError("k must be >= 1")
-    if use_blas is None:
-        use_blas = exact_integer_inputs(q, x)
     a = norm2(q)
     best_i = np.full((nq, k), -1, dtype=np.int64)
     best_s = np.full((nq, k), -np.inf, dtype=np.float64)
     for lo in range(0, n, chunk):
         hi = min(n, lo + chunk)
-        s = cosine_scores(q, x[lo:hi], a=a, b=norm2(x[lo:hi]), use_blas=use_blas)
+        # one chunk in binary64 at a time (a large database need not fit
+        # twice in memory); the BLAS product is taken for a chunk only when
+        # it is provably equal to the sequential loop there, so the choice
+        # never changes a score
+        xc = np.asarray(x[lo:hi], dtype=np.float64)
+        blas = exact_integer_inputs(q, xc) if use_blas is None else use_blas
+        s = cosine_scores(q, xc, a=a, b=norm2(xc), use_blas=blas)
         ci, cs = _topk_rows(s, np.arange(lo, hi, dtype=np.int64), k, exclude)
         best_i, best_s = _merge(best_i, best_s, ci, cs, k)
     dist = np.where(best_i >= 0, 1.0 - best_s, np.inf)

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "fs_db_set_tuning": [P, ctypes.POINTER(_Tuning)],
     "fs_db_set_metric": [P, ctypes.c_int, P],
     "fs_db_get_tuning": [P, ctypes.POINTER(_Tuning)],
+    "fs_db_set_wait_test": [P, I32, ctypes.c_uint32],
     "fs_profile_enable": [I32],
     "fs_profile_read": [I32, ctypes.POINTER(_Profile)],
 }
@@ -320,6 +321,14 @@ def fs_db_get_tuning(db: Database) -> dict:
     t = _Tuning()
     _check(lib().fs_db_get_tuning(db.handle, ctypes.byref(t)))
     return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
+
+
+def fs_db_set_wait_test(db: Database, withhold_first_load: bool, wait_limit_us: int = 0):
+    """Test aid: later tensor-core scans on `db` skip their first tile copy
+    so their bounded waits run out after `wait_limit_us` (0: the default 2 s);
+    fs_db_check then reports FS_ETIMEOUT."""
+    _check(lib().fs_db_set_wait_test(db.handle, 1 if withhold_first_load else 0,
+                                     int(wait_limit_us)))
 
 
 def fs_db_destroy(db: Database):

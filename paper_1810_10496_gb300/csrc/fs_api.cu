@@ -53,6 +53,8 @@ struct fs_db {
     float* row_mag = nullptr;       // [n] |z| or sum |z_i|
     float* mag_max_dev = nullptr;   // [n_seg]
     std::vector<float> mag_max;     // host copy
+    uint64_t wait_ns = 0;           // limit of the scan's bounded waits (0: 2 s)
+    int withhold_load = 0;          // test aid (fs_db_set_wait_test)
 };
 
 namespace {
@@ -174,9 +176,12 @@ Bounds score_bounds(const fs_db* db, double r_xmax) {
     const double u = std::ldexp(1.0, -24);
     const int m = (int)ceil_div(db->fu, 32);
     auto gamma = [u](double n) { return n * u / (1.0 - n * u); };
-    // |computed 1/||x|| * ||x|| - 1| <= eta: FMA sums of m squares per lane,
-    // a 5-level butterfly, a square root and a reciprocal
-    const double eta = ((m + 5) * 0.5 + 2.0) * u * 1.01;
+    // |computed 1/||x|| * ||x|| - 1| <= eta: FMA sums of m_norm squares per
+    // lane (a 32-stride element per lane, or four consecutive elements per
+    // 128-element block with 128-bit loads), a 5-level butterfly, a square
+    // root and a reciprocal
+    const int m_norm = std::max(m, 4 * (int)ceil_div(db->f, 128));
+    const double eta = ((m_norm + 5) * 0.5 + 2.0) * u * 1.01;
     // |u_q . u_x - s| for the FP32 unit vectors (each element also rounded)
     const double th = 2.0 * u + u * u;
     const double e_norm = (2.0 * eta + eta * eta) * (1.0 + th) + th;
@@ -476,6 +481,9 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.fb_count = (int32_t*)(ws + L.counters);
     c.work_counter = c.fb_count + 1;
     c.fb2_count = c.fb_count + 2;
+    c.aborted = c.fb_count + 3;
+    c.wait_ns = db->wait_ns;
+    c.withhold_load = db->withhold_load;
     c.fb_list = (int32_t*)(ws + L.fb_list);
     c.fb2_list = (int32_t*)(ws + L.fb2_list);
     c.cand_fb = (uint64_t*)(ws + L.cand_fb);
@@ -544,6 +552,17 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
 }  // namespace
 
 namespace fsk {
+fs_status search_scratch_bytes(const fs_db* db, int32_t nq, const int32_t* q_seg_off,
+                               const int32_t* k, size_t* bytes) {
+    if (!db || !bytes) return fail(FS_EINVAL, "db and bytes must be non-NULL");
+    if (nq < 0) return fail(FS_EINVAL, "nq=%d is negative", nq);
+    Plan pl;
+    fs_status st = make_plan(db, nq, q_seg_off, k, pl);
+    if (st != FS_OK) return st;
+    *bytes = make_layout(db, nq, pl).total;
+    return FS_OK;
+}
+
 fs_status set_error(fs_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -770,6 +789,15 @@ fs_status fs_db_set_tuning(fs_db* db, const fs_tuning* t) {
     if (t->scan_pairs < -1 || t->scan_pairs > 1)
         return fail(FS_EINVAL, "scan_pairs=%d is outside -1..1", t->scan_pairs);
     db->tune = *t;
+    return FS_OK;
+}
+
+fs_status fs_db_set_wait_test(fs_db* db, int32_t withhold_first_load, uint32_t wait_limit_us) {
+    if (!db) return fail(FS_EINVAL, "db is NULL");
+    if (wait_limit_us > 2000000u)
+        return fail(FS_EINVAL, "wait_limit_us=%u is above 2,000,000", wait_limit_us);
+    db->withhold_load = withhold_first_load != 0;
+    db->wait_ns = (uint64_t)wait_limit_us * 1000ull;
     return FS_OK;
 }
 

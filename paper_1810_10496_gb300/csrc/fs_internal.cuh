@@ -23,6 +23,10 @@ constexpr int kListTTiny = 4;     // list size when every k <= 4 (a tuning choic
 constexpr int kWindow = 64;       // candidates the rerank takes per query
 constexpr int kQTile = 128;       // queries per scan work item
 constexpr int kFbChunks = 32;     // row chunks per query in the exact fallback
+// Devices whose kernel attributes are cached (cudaFuncSetAttribute acts on
+// the current device's context only, so every cache of it is per device;
+// a device beyond this count sets its attributes on every launch).
+constexpr int kMaxDevices = 64;
 
 // device status bits (fs_db::status)
 constexpr uint32_t kStBadFeature = 1u;     // non-finite / out-of-range value
@@ -184,7 +188,8 @@ struct CallView {
     float* q_resid;           // [nq]
     uint64_t* cand;           // candidate lists
     int32_t* fb_count;        // queries sent to the FP32 rescan (fb_count[1] is the
-                              // scan scheduler, fb_count[2] is fb2_count)
+                              // scan scheduler, fb_count[2] is fb2_count, fb_count[3]
+                              // is `aborted`)
     int32_t* fb_list;         // [nq]
     int32_t* fb2_count;       // queries sent on to the binary64 scan
     int32_t* fb2_list;        // [nq]
@@ -192,6 +197,11 @@ struct CallView {
     double* fb_score;         // [nq][kFbChunks][FS_MAX_K]
     int32_t* fb_index;        // [nq][kFbChunks][FS_MAX_K]
     int32_t* work_counter;    // dynamic scan scheduler
+    int32_t* aborted;         // nonzero once a bounded wait of this call's scan gave up:
+                              // its candidate lists are incomplete, so the selection
+                              // writes padding instead of reading them
+    uint64_t wait_ns;         // limit of every bounded wait of the scan (0: kWaitLimitNs)
+    int32_t withhold_load;    // test aid: every scan block skips its first row-tile load
     uint32_t* shared_thr;     // [nq] per query: a score below which no row can be
                               // among the k nearest (order-mapped bits)
     const int32_t* exclude;   // [nq] or NULL
@@ -231,6 +241,10 @@ cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_o
 
 // fs_api.cu: records the message fs_last_error() returns on this thread
 fs_status set_error(fs_status st, const char* fmt, ...);
+// fs_api.cu: the workspace bytes one search call with exactly these
+// arguments uses (fs_workspace_size sizes for any k, so it can be larger)
+fs_status search_scratch_bytes(const fs_db* db, int32_t nq, const int32_t* q_seg_off,
+                               const int32_t* k, size_t* bytes);
 
 // scan_fp32.cu
 constexpr int kFp32TileRows = 128;

@@ -46,8 +46,9 @@ extern "C" fs_status fs_knn_noalloc(const fs_db* db, const float* q, int32_t nq,
                                     const int32_t* exclude, int32_t* idx, float* dist,
                                     void* stream) {
     if (!db) return fsk::set_error(FS_EINVAL, "db is NULL");
+    // the scratch this call's own layout takes (its k and list length)
     size_t need = 0;
-    fs_status st = fs_workspace_size(db, nq, q_seg_off, &need);
+    fs_status st = fsk::search_scratch_bytes(db, nq, q_seg_off, k, &need);
     if (st != FS_OK) return st;
     if (need > kScratchBytes)
         return fsk::set_error(FS_ENOMEM,

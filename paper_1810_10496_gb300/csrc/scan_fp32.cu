@@ -12,6 +12,8 @@
 // persistent blocks take items from an atomic counter. Items of one row chunk
 // are numbered consecutively over the query tiles, so blocks that run at the
 // same time read the same rows and share them through L2.
+#include <mutex>
+
 #include "fs_internal.cuh"
 
 namespace fsk {
@@ -265,22 +267,30 @@ k_scan_fp32(DbView db, CallView call) {
 
 }  // namespace
 
+// Sets the kernels' dynamic shared-memory limit on the current device and
+// returns the resident blocks per SM. Both belong to the current device's
+// context, so they are kept per device.
 int scan_fp32_ctas_per_sm() {
-    static int cached = -1;
-    if (cached < 0) {
-        cudaFuncSetAttribute(k_scan_fp32<FS_COSINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(Smem));
-        cudaFuncSetAttribute(k_scan_fp32<FS_EUCLIDEAN>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        cudaFuncSetAttribute(k_scan_fp32<FS_MANHATTAN>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_fp32<FS_COSINE>, THREADS,
-                                                          sizeof(Smem)) != cudaSuccess || nb < 1)
-            nb = 1;
-        cached = nb;
+    static std::mutex mu;
+    static int cached[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    std::lock_guard<std::mutex> g(mu);
+    if (dev >= 0 && dev < kMaxDevices && cached[dev] > 0) return cached[dev];
+    cudaFuncSetAttribute(k_scan_fp32<FS_COSINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(Smem));
+    cudaFuncSetAttribute(k_scan_fp32<FS_EUCLIDEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(Smem));
+    cudaFuncSetAttribute(k_scan_fp32<FS_MANHATTAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(Smem));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_fp32<FS_COSINE>, THREADS,
+                                                      sizeof(Smem)) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
     }
-    return cached;
+    if (dev >= 0 && dev < kMaxDevices) cached[dev] = nb;
+    return nb;
 }
 
 cudaError_t launch_scan_fp32(const DbView& db, const CallView& call, int grid, cudaStream_t st) {

@@ -37,6 +37,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "fs_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -78,9 +80,9 @@ struct Bars {
 // items left). False when a wait gave up.
 __device__ __forceinline__ bool claim_item(Bars& bars, volatile int32_t* item_q,
                                            const CallView& call, uint32_t n,
-                                           volatile int* abort_flag, int64_t& item) {
+                                           volatile int* abort_flag, uint64_t wlim, int64_t& item) {
     const uint32_t slot = n % kItemQ, ph = (n / kItemQ) & 1;
-    if (!mbar_wait(smem_u32(&bars.item_empty[slot]), ph ^ 1, abort_flag)) return false;
+    if (!mbar_wait(smem_u32(&bars.item_empty[slot]), ph ^ 1, abort_flag, wlim)) return false;
     int32_t v = atomicAdd(call.work_counter, 1);
     if ((int64_t)v >= call.total_items) v = -1;
     item_q[slot] = v;
@@ -92,9 +94,9 @@ __device__ __forceinline__ bool claim_item(Bars& bars, volatile int32_t* item_q,
 // Another role reads the n-th item; the caller then arrives on
 // item_empty[n % kItemQ] (once per thread or warp counted there).
 __device__ __forceinline__ bool take_item(Bars& bars, const volatile int32_t* item_q, uint32_t n,
-                                          volatile int* abort_flag, int64_t& item) {
+                                          volatile int* abort_flag, uint64_t wlim, int64_t& item) {
     const uint32_t slot = n % kItemQ, ph = (n / kItemQ) & 1;
-    if (!mbar_wait(smem_u32(&bars.item_full[slot]), ph, abort_flag)) return false;
+    if (!mbar_wait(smem_u32(&bars.item_full[slot]), ph, abort_flag, wlim)) return false;
     item = item_q[slot];
     return true;
 }
@@ -134,10 +136,10 @@ __device__ __forceinline__ Item decode(const CallView& call, int64_t item, uint3
 }
 
 // A bounded wait that ignores the abort flag (used to drain on the way out).
-__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64_t wlim) {
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > kWaitLimitNs) break;
+        if (globaltimer() - t0 > wlim) break;
 }
 
 // PAIR: a cluster of two CTAs shares every tile (cta_group::2). Each CTA
@@ -171,6 +173,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     const int64_t unit0 = PAIR ? blockIdx.x / 2 : blockIdx.x;
     const int64_t nunits = PAIR ? gridDim.x / 2 : gridDim.x;
     constexpr uint16_t kPairMask = 0x3;
+    const uint64_t wlim = call.wait_ns ? call.wait_ns : kWaitLimitNs;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -219,11 +222,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (PAIR) {
                     if (item >= call.total_items) break;
                 } else {
-                    ok = claim_item(bars, item_q, call, n, &abort_flag, item);
+                    ok = claim_item(bars, item_q, call, n, &abort_flag, wlim, item);
                     if (!ok || item < 0) break;
                 }
                 const Item w = decode(call, item, rank, PAIR);
-                ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag);
+                ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag, wlim);
                 if (!ok) break;
                 mbar_arrive_expect_tx(smem_u32(&bars.a_full), kblocks * kABlockBytes);
                 for (int kb = 0; kb < kblocks; ++kb)
@@ -236,8 +239,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         (int32_t)(w.row_begin + (int64_t)t * BN + (PAIR ? rank * (BN / 2) : 0));
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
-                        ok = mbar_wait(smem_u32(&bars.empty[s]), ph ^ 1, &abort_flag);
+                        ok = mbar_wait(smem_u32(&bars.empty[s]), ph ^ 1, &abort_flag, wlim);
                         if (!ok) break;
+                        // test aid: the first ring slot is never filled, so the MMA
+                        // issuer's wait for it runs out (nothing is left in flight)
+                        if (call.withhold_load && it == 0) continue;
                         mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kBStage);
                         tma_load_2d(b_smem + s * kBStage, &map_x, smem_u32(&bars.full[s]),
                                     kb * kElemsPerKBlock, row);
@@ -245,10 +251,12 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 }
             }
             if (!ok) {
-                // let the copies already issued land before the block exits
+                // let the copies already issued land before the block exits (the
+                // withheld slot, if any, has nothing to wait for)
                 for (uint32_t j = (it >= (uint32_t)stages ? it - stages : 0); j < it; ++j)
-                    drain_wait(smem_u32(&bars.full[j % stages]), (j / stages) & 1);
-                if (a_loads > 0) drain_wait(smem_u32(&bars.a_full), (a_loads - 1) & 1);
+                    if (!(call.withhold_load && j == 0))
+                        drain_wait(smem_u32(&bars.full[j % stages]), (j / stages) & 1, wlim);
+                if (a_loads > 0) drain_wait(smem_u32(&bars.a_full), (a_loads - 1) & 1, wlim);
             }
         }
     } else if (warp == 1 && (!PAIR || leader)) {
@@ -267,26 +275,26 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (PAIR) {
                     if (item >= call.total_items) break;
                 } else {
-                    ok = take_item(bars, item_q, n, &abort_flag, item);
+                    ok = take_item(bars, item_q, n, &abort_flag, wlim, item);
                     if (!ok) break;
                     mbar_arrive(smem_u32(&bars.item_empty[n % kItemQ]));
                     if (item < 0) break;
                 }
                 const Item w = decode(call, item, rank, PAIR);
-                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
-                if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pa_full), ic & 1, &abort_flag);
+                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag, wlim);
+                if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pa_full), ic & 1, &abort_flag, wlim);
                 if (!ok) break;
                 tc_fence_after();
                 for (int t = 0; ok && t < w.ntiles; ++t, ++tcount) {
                     const uint32_t acc = tcount % kAccs, aph = (tcount / kAccs) & 1;
-                    ok = mbar_wait(smem_u32(&bars.tmem_empty[acc]), aph ^ 1, &abort_flag);
+                    ok = mbar_wait(smem_u32(&bars.tmem_empty[acc]), aph ^ 1, &abort_flag, wlim);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d = tmem_base + acc * BN;
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
-                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
-                        if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pfull[s]), ph, &abort_flag);
+                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag, wlim);
+                        if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pfull[s]), ph, &abort_flag, wlim);
                         if (!ok) break;
                         tc_fence_after();
 #pragma unroll
@@ -314,7 +322,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             }
             // every MMA this thread issued has finished before TMEM is freed
             commit(bars.drain);
-            drain_wait(smem_u32(&bars.drain), 0);
+            drain_wait(smem_u32(&bars.drain), 0, wlim);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ load forwarder
@@ -326,20 +334,20 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             bool ok = true;
             for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
                 const Item w = decode(call, item, rank, PAIR);
-                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag);
+                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag, wlim);
                 if (!ok) break;
                 mbar_arrive_cluster(r_pa_full);
                 for (int t = 0; ok && t < w.ntiles; ++t) {
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
-                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag);
+                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag, wlim);
                         if (!ok) break;
                         mbar_arrive_cluster(mapa_shared(smem_u32(&bars.pfull[s]), 0));
                     }
                 }
             }
             // the leader's last commit: every MMA writing this CTA's TMEM is done
-            drain_wait(smem_u32(&bars.drain), 0);
+            drain_wait(smem_u32(&bars.drain), 0, wlim);
         }
     } else {
         // ------------------------------------------------ epilogue
@@ -358,7 +366,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             if (PAIR) {
                 if (item >= call.total_items) break;
             } else {
-                ok = take_item(bars, item_q, n, &abort_flag, item);
+                ok = take_item(bars, item_q, n, &abort_flag, wlim, item);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 __syncwarp();
@@ -401,11 +409,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         sx[acc][j] = r < w.row_end ? db.scale[r] : 0.0f;
                     }
                     mbar_arrive(smem_u32(&bars.sx_ready[acc]));
-                    ok = mbar_wait(smem_u32(&bars.sx_ready[acc]), aph, &abort_flag);
+                    ok = mbar_wait(smem_u32(&bars.sx_ready[acc]), aph, &abort_flag, wlim);
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
                 }
-                ok = mbar_wait(smem_u32(&bars.tmem_full[acc]), aph, &abort_flag);
+                ok = mbar_wait(smem_u32(&bars.tmem_full[acc]), aph, &abort_flag, wlim);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
@@ -508,7 +516,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         }
     }
 
-    if (abort_flag && threadIdx.x == 0) atomicOr(db.status, kStTimeout);
+    if (abort_flag && threadIdx.x == 0) {
+        atomicOr(db.status, kStTimeout);
+        atomicOr(call.aborted, 1);
+    }
     tc_fence_before();
     __syncthreads();
     // no arrival or MMA of one CTA of a pair may reach the other after it exits
@@ -575,16 +586,23 @@ cudaError_t make_code_map(CUtensorMap* map, const void* ptr, int64_t rows, int c
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Raises the kernel's dynamic shared-memory limit to `smem` on the current
+// device. The attribute belongs to that device's context, so the largest
+// size set so far is remembered per device.
 template <bool FP8, int LT, bool PAIR>
 cudaError_t set_smem(size_t smem) {
-    static size_t attr_bytes = 0;   // the largest dynamic size set so far
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_scan_tc<FP8, LT, PAIR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_bytes = smem;
-    }
-    return cudaSuccess;
+    static std::mutex mu;
+    static size_t attr_bytes[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    size_t* have = (dev >= 0 && dev < kMaxDevices) ? &attr_bytes[dev] : nullptr;
+    if (have && smem <= *have) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_scan_tc<FP8, LT, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e == cudaSuccess && have) *have = smem;
+    return e;
 }
 
 template <bool FP8, int LT, bool PAIR>
@@ -634,9 +652,13 @@ cudaError_t launch_lists(bool fp8, int list_t, const DbView& db, const CallView&
 // Pairs of CTAs that can be resident at once (a cluster occupies two SMs of
 // one GPU processing cluster; not every SM need find a partner), 0 on error.
 int scan_tc_pair_slots(bool fp8, int kblocks) {
-    static int cached[2][kMaxKBlocks + 1] = {};
+    static std::mutex mu;
+    static int cached[kMaxDevices][2][kMaxKBlocks + 1] = {};   // per device
     if (kblocks < 1 || kblocks > kMaxKBlocks) return 0;
-    int& c = cached[fp8 ? 1 : 0][kblocks];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    std::lock_guard<std::mutex> g(mu);
+    int& c = cached[dev][fp8 ? 1 : 0][kblocks];
     if (c > 0) return c;
     const int stages = scan_tc_stages(kblocks, fp8, true);
     const size_t smem = scan_tc_smem_bytes(kblocks, stages, true);

@@ -51,6 +51,7 @@ __global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* dst_
     if (i == 0 && fb_count) {
         fb_count[0] = 0;    // queries for the FP32 rescan
         fb_count[2] = 0;    // queries for the binary64 scan
+        fb_count[3] = 0;    // the scan has not given up
         *work_counter = 0;
     }
 }
@@ -134,6 +135,9 @@ __device__ __forceinline__ void write_padding(const CallView& call, int q, int f
 
 constexpr int kSelWarps = 8;
 constexpr int kRescoreRows = 4;   // window rows the FP32 rescoring reads at once
+// FP32 distances below this are replaced by the binary64 one (near
+// duplicates; above it the FP32 value is within 3e-6 relative)
+constexpr float kExactDist = 4e-3f;
 
 struct SelShared {
     int32_t widx[kSelWarps][kWindow];     // window rows (segment-local), scan order
@@ -388,17 +392,31 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
         }
         __syncwarp();
     }
-    // 8. the first k places
+    // 8. the first k places. A place outside a near-tie cluster reports the
+    //    FP32 distance 1/2 |u_q - u_x|^2 unless that is below kExactDist: the
+    //    rounding of the unit vectors' elements (2^-24 relative each) moves it
+    //    by up to about 2^-23 sqrt(2d), more than 1e-5 d once d is below about
+    //    3e-4, so near duplicates take the binary64 cosine (d = 1 - s).
     const int nout = min(nw, k);
+    int nexact = 0;
     for (int c = lane; c < nout; c += 32) {
         call.out_idx[out0 + c] = sh.sidx[wid][c];
         float d = sh.sdist[wid][c];
-        if (sh.tie[wid][c]) d = (float)(1.0 - sh.s64[wid][c]);
+        if (sh.tie[wid][c]) {
+            d = (float)(1.0 - sh.s64[wid][c]);
+        } else if (d < kExactDist) {
+            const int64_t row = p.row0 + sh.sidx[wid][c];
+            const float* qr = call.q_raw + (int64_t)q * db.f;
+            d = (float)(1.0 - exact_cosine_ab(qr, db.raw + row * db.f, db.f, db.b64[row]));
+            ++nexact;
+        }
         call.out_dist[out0 + c] = d;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nexact += __shfl_xor_sync(kFull, nexact, o);
     if (lane == 0) {
         atomicAdd(&stats[kStatRerank], (unsigned long long)nw);
-        atomicAdd(&stats[kStatFp64], (unsigned long long)nfp);
+        atomicAdd(&stats[kStatFp64], (unsigned long long)(nfp + nexact));
         atomicAdd(&stats[kStatNearTies], (unsigned long long)ncl);
     }
     return nout;
@@ -413,7 +431,11 @@ k_select(DbView db, CallView call) {
     __syncthreads();
     const int q = blockIdx.x * kSelWarps + wid;
 
-    if (q < call.nq) {
+    if (q < call.nq && *call.aborted) {
+        // a bounded wait of the scan gave up (FS_ETIMEOUT in the status word):
+        // its candidate lists are incomplete, so no answer is given
+        write_padding(call, q, 0);
+    } else if (q < call.nq) {
         const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;

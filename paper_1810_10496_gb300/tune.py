@@ -7,10 +7,13 @@ every candidate returns the same answers as the defaults, and keeps the
 fastest. The selection is exact, so a tuning can only change the time; a
 candidate whose answers differ is a library error and raises.
 
-Results are cached in a JSON file keyed by the device name, the precision,
-the feature count and power-of-two buckets of the rows, queries and
-segments, plus the largest k, so a later process with a batch of the same
-shape applies the choice without timing again.
+Results are cached in a JSON file keyed by a schema version, the device
+name, the precision, the similarity metric, the feature count and
+power-of-two buckets of the rows, queries and segments, plus the largest k,
+so a later process with a batch of the same shape applies the choice without
+timing again. The schema version changes whenever the meaning of a tuning
+parameter changes, so entries written under an older meaning are timed
+again rather than applied.
 """
 from __future__ import annotations
 
@@ -26,6 +29,9 @@ DEFAULT_CACHE = os.environ.get(
 ITEMS_PER_BLOCK = (1, 2, 4, 8, 16)
 LIST_LEN = (4, 8, 16)
 L2_SHARE_PCT = (25, 50, -1)
+# bumped whenever a tuning parameter changes meaning (2: scan items are
+# claimed dynamically, so items_per_block sets the item length only)
+SCHEMA = 2
 
 
 def candidates(prec: str, n_seg: int, k_max: int) -> list[dict]:
@@ -67,9 +73,9 @@ def _bucket(v: int) -> int:
 
 
 def shape_key(device: str, prec: str, f: int, n_rows: int, nq: int, n_seg: int,
-              k_max: int) -> str:
-    return (f"{device}|{prec}|F{f}|N{_bucket(n_rows)}|Q{_bucket(nq)}|S{_bucket(n_seg)}"
-            f"|K{k_max}")
+              k_max: int, metric: str = "cosine") -> str:
+    return (f"v{SCHEMA}|{device}|{prec}|{metric}|F{f}|N{_bucket(n_rows)}|Q{_bucket(nq)}"
+            f"|S{_bucket(n_seg)}|K{k_max}")
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
@@ -134,7 +140,7 @@ def autotune(db, q, k, q_seg_off=None, reps: int = 5, cache_path: str | None = D
     kk = np.broadcast_to(np.asarray(k, dtype=np.int32), (db.n_seg,))
     k_max = int(kk.max())
     key = shape_key(torch.cuda.get_device_name(q.device), db.prec, db.f, db.n, nq, db.n_seg,
-                    k_max)
+                    k_max, db.metric)
     cache = load_cache(cache_path) if cache_path else {}
     if not force and key in cache:
         fs.fs_db_set_tuning(db, cache[key]["tuning"])

@@ -301,14 +301,14 @@ def test_errors_are_reported(fs):
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_full_scale_sampled(fs, prec):
     """1,048,576 x 128 database, 4,096 queries, k = 3 (the FP32-at-scale
-    workload), in the launch configuration the benchmark times; 48 sampled
+    workload), in the launch configuration the benchmark times; 256 sampled
     queries are checked against the oracle on the whole database."""
     import torch
     w = fsgen.make("fp32_scale", workers=8)
     db = build_db(fs, w.x, w.seq_off, w.seq_ids, prec)
     idx, dist, seqs, lens, _ = run(fs, db, w.queries, 3)
     rng = np.random.default_rng(0)
-    pick = np.sort(rng.choice(w.q, size=48, replace=False))
+    pick = np.sort(rng.choice(w.q, size=256, replace=False))
     i_o, d_o, s_o, l_o = oracle.recommend(w.x, w.queries[pick], 3, w.seq_off, w.seq_ids, 128)
     assert_same(idx[pick], dist[pick], i_o, d_o)
     assert np.array_equal(seqs[pick], s_o) and np.array_equal(lens[pick], l_o)
@@ -391,3 +391,49 @@ def test_mid_size_many_query_tiles(fs, prec):
     i_o, d_o, s_o, l_o = oracle.recommend(w.x, w.queries, 3, w.seq_off, w.seq_ids, 128)
     assert_same(idx, dist, i_o, d_o)
     assert np.array_equal(seqs, s_o) and np.array_equal(lens, l_o)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_near_duplicates_relative_distance(fs, prec):
+    """Rows that differ from a query in one feature (distances of about 1e-8
+    to 2e-4) and a row parallel to it (distance 0): the distances must hold
+    1e-5 relative with no absolute floor, and 0 exactly."""
+    w = fsgen.make("tiny_k3", n=6000, q=40, f=128, seed=29)
+    x = w.x.copy()
+    qy = 16.0 * w.queries                     # larger counts: one count is a small change
+    for i in range(40):
+        base = qy[i]
+        j = 150 * i
+        top = int(np.argmax(base))
+        x[j] = base
+        x[j, top] += 1.0                      # one count more on the largest feature
+        x[j + 1] = base
+        x[j + 1, (top + 1) % 128] += 3.0      # three counts more elsewhere
+        x[j + 2] = 2.0 * base                 # parallel: s = 1 exactly
+    db = build_db(fs, x, w.seq_off, w.seq_ids, prec)
+    idx, dist, *_ = run(fs, db, qy, 3)
+    i_o, d_o, _ = oracle.knn(x, qy, 3)
+    assert np.array_equal(idx, i_o)
+    assert np.all(d_o[:, 0] == 0.0) and np.all(dist[:, 0] == 0.0)
+    err = np.abs(dist.astype(np.float64) - d_o)
+    assert np.all(err <= 1e-5 * d_o), float(np.max(err / np.maximum(d_o, 1e-300)))
+    assert np.all(d_o[:, 1:] < 1e-3)          # the case is what it says
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_fp8_certified_path(fs, k):
+    """Queries that are scaled copies of database rows, far from every other
+    row: FP8's candidate lists certify their answers, so the certified path
+    (not the exact fallback) gives them, and they must equal the oracle's."""
+    w = fsgen.make("tiny_k3", n=20000, q=1, f=128, seed=19)
+    pick = np.arange(3, 20000, 97)[:200]
+    qy = 3.0 * w.x[pick]
+    db = build_db(fs, w.x, w.seq_off, w.seq_ids, "fp8")
+    fs.fs_db_stats(db, reset=True)
+    idx, dist, seqs, lens, _ = run(fs, db, qy, k)
+    i_o, d_o, s_o, l_o = oracle.recommend(w.x, qy, k, w.seq_off, w.seq_ids, 128)
+    assert_same(idx, dist, i_o, d_o)
+    assert np.array_equal(seqs, s_o) and np.array_equal(lens, l_o)
+    st = fs.fs_db_stats(db)
+    assert st["queries"] == len(pick) and st["certified"] + st["fallback"] == len(pick)
+    assert st["certified"] >= (0.9 if k == 1 else 0.5) * len(pick), st

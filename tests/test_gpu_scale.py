@@ -1,0 +1,138 @@
+"""Parity at the full sizes of the two large workloads, in the launch
+configuration the benchmark times.
+
+* 16,777,216 x 256 database, 8,192 queries, k = 3: 2^32 feature elements, so
+  every element offset past row 8,388,607 needs 64-bit arithmetic, the BF16
+  codes span 8.6 GB behind one TMA map, and the chunk planner caps the chunks
+  in flight at a share of L2. 64 sampled queries are checked against the
+  oracle on all 16.7 M rows; every query's row list must be valid.
+* 512 databases of log-uniform size (1,000-200,000 rows x 128), 1-256
+  queries each, k in {1, 3}, searched in one call with the plan tuning the
+  benchmark picks and as a CUDA graph replay: every query of the 8 largest
+  databases and the first query of every other database against the oracle
+  on its own database.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import fsgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-5, 1e-6
+WORKERS = min(16, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def fs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_10496_gb300 import build
+    build.build()
+    import paper_1810_10496_gb300 as m
+    return m
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check(idx_g, dist_g, seq_g, len_g, i_o, d_o, s_o=None, l_o=None):
+    k = i_o.shape[1]
+    assert np.array_equal(idx_g[:, :k], i_o), (idx_g[:, :k], i_o)
+    err = np.abs(dist_g[:, :k].astype(np.float64) - d_o)
+    assert np.all(err <= RTOL * np.abs(d_o) + ATOL), float(err.max())
+    if s_o is not None:
+        assert np.array_equal(seq_g[:, :k], s_o) and np.array_equal(len_g[:, :k], l_o)
+
+
+@pytest.fixture(scope="module")
+def precision():
+    w = fsgen.make("precision", workers=WORKERS)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(w.q, size=64, replace=False))
+    ref = oracle.recommend(w.x, w.queries[pick], 3, w.seq_off, w.seq_ids, 128)
+    return w, pick, ref
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_precision_config_sampled(fs, precision, prec):
+    import torch
+    w, pick, (i_o, d_o, s_o, l_o) = precision
+    x = _dev(w.x)
+    db = fs.fs_build_db(x, _dev(w.seq_off), _dev(w.seq_ids), prec=prec)
+    del x
+    fs.fs_db_stats(db, reset=True)
+    idx, dist, seqs, lens, _ = fs.fs_recommend(db, _dev(w.queries), 3)
+    torch.cuda.synchronize()
+    fs.fs_db_check(db)
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    _check(idx[pick], dist[pick], seqs[pick].cpu().numpy(), lens[pick].cpu().numpy(),
+           i_o, d_o, s_o, l_o)
+    st = fs.fs_db_stats(db)
+    assert st["queries"] == w.q and st["certified"] + st["fallback"] == w.q
+    # every query: distinct rows in range, ordered by distance
+    assert np.all((idx >= 0) & (idx < w.n))
+    assert np.all(idx[:, 0] != idx[:, 1]) and np.all(idx[:, 1] != idx[:, 2])
+    assert np.all(np.diff(dist, axis=1) >= -1e-6) and np.all((dist >= 0) & (dist <= 1))
+    db.close()
+    torch.cuda.empty_cache()
+
+
+def test_batching_config(fs):
+    import torch
+    w = fsgen.make("batching", workers=WORKERS)
+    ks = np.array(w.k, dtype=np.int32)
+    so, qo = w.seg_off, w.q_seg_off
+    x = _dev(w.x)
+    db = fs.fs_build_db(x, _dev(w.seq_off), _dev(w.seq_ids), seg_off=so, prec="bf16")
+    del x
+    # the plan the benchmark's autotuner picks for this batch
+    fs.fs_db_set_tuning(db, {"items_per_block": 1, "list_len": 16})
+    q = _dev(w.queries)
+    k_max = int(ks.max())
+    ws = torch.empty(fs.fs_workspace_size(db, w.q, qo), dtype=torch.uint8, device="cuda")
+    out = dict(idx=torch.empty((w.q, k_max), dtype=torch.int32, device="cuda"),
+               dist=torch.empty((w.q, k_max), dtype=torch.float32, device="cuda"),
+               seq_out=torch.empty((w.q, k_max, 128), dtype=torch.int16, device="cuda"),
+               seq_len=torch.empty((w.q, k_max), dtype=torch.int32, device="cuda"))
+    fs.fs_recommend(db, q, ks, q_seg_off=qo, workspace=ws, **out)
+    torch.cuda.synchronize()
+    fs.fs_db_check(db)
+    eager = {k: v.cpu().numpy() for k, v in out.items()}
+    for v in out.values():
+        v.fill_(0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fs.fs_recommend(db, q, ks, q_seg_off=qo, workspace=ws, **out)
+    g.replay()
+    torch.cuda.synchronize()
+    fs.fs_db_check(db)
+    for k, v in out.items():
+        assert np.array_equal(v.cpu().numpy(), eager[k]), k
+
+    sizes = np.diff(so)
+    largest = set(np.argsort(-sizes, kind="stable")[:8].tolist())
+    checked = 0
+    for s in range(len(sizes)):
+        a, b = int(qo[s]), int(qo[s + 1])
+        if a == b:
+            continue
+        if s not in largest:
+            b = a + 1
+        lo, hi = int(so[s]), int(so[s + 1])
+        kk = int(ks[s])
+        off = w.seq_off[lo:hi + 1] - w.seq_off[lo]
+        ids = w.seq_ids[w.seq_off[lo]:w.seq_off[hi]]
+        i_o, d_o, s_o, l_o = oracle.recommend(w.x[lo:hi], w.queries[a:b], kk, off, ids, 128)
+        _check(eager["idx"][a:b], eager["dist"][a:b], eager["seq_out"][a:b],
+               eager["seq_len"][a:b], i_o, d_o, s_o, l_o)
+        assert np.all(eager["idx"][a:b, kk:] == -1)
+        checked += b - a
+    assert checked >= 512
+    db.close()

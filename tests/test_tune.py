@@ -31,7 +31,9 @@ def test_shape_key_buckets():
     assert a == b and "N1048576" in a and "Q4096" in a
     assert a != tune.shape_key("GB300", "bf16", 128, 1_048_577, 4096, 1, 3)
     assert a != tune.shape_key("GB300", "fp8", 128, 1_048_576, 4096, 1, 3)
-    assert tune.shape_key("x", "bf16", 8, 0, 0, 1, 1).startswith("x|bf16|F8|N0|Q0|S1")
+    assert tune.shape_key("x", "bf16", 8, 0, 0, 1, 1).startswith(f"v{tune.SCHEMA}|x|bf16|cosine|F8|N0|Q0|S1")
+    # the metric selects a different scan kernel: its own entry
+    assert a != tune.shape_key("GB300", "bf16", 128, 1_000_000, 4000, 1, 3, "euclidean")
 
 
 def test_cache_round_trip(tmp_path):
