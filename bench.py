@@ -219,7 +219,7 @@ def run_reference(args):
     world, rank, _ = setup_dist()
     if rank != 0:
         return 0
-    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
+    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q, n_db=args.n_db)
     # each step a bounded sample: about 4 s of oracle work
     nq = args.ref_sample if args.ref_sample else oracle_sample_size(w, 4.0, 1, 32)
     times, pairs = [], 0
@@ -400,7 +400,7 @@ def run_ours(args):
         return run_serving(args, fs, torch, dev, world, rank, local)
 
     t0 = time.perf_counter()
-    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q)
+    w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q, n_db=args.n_db)
     log(f"[rank {rank}] workload generated in {time.perf_counter() - t0:.1f} s")
     ks = np.array(w.k, dtype=np.int32)
     k_max = int(ks.max())
@@ -558,7 +558,7 @@ def run_ours(args):
                 "peak_source": f"{peak_src} bf16 burst" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # the captured figure holds for the captured configuration only
-    same_config = args.n is None and args.q is None and not tuned
+    same_config = args.n is None and args.q is None and args.n_db is None and not tuned
     roof["traffic"] = TRAFFIC_BYTES.get((f"scan_{prec}", args.workload, prec)) if same_config else None
     roof["kernel"] = f"scan ({prec})"
     roof["kernel_ms"] = scan_ms
@@ -669,6 +669,8 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="database rows instead of the workload's (bounded profiling cases)")
     ap.add_argument("--q", type=int, default=None, help="queries instead of the workload's")
+    ap.add_argument("--n-db", type=int, default=None,
+                    help="batching: databases instead of 512 (bounded profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="queries of the CPU-oracle sample (default: about 15 s of work)")
     ap.add_argument("--rate", type=float, default=500_000,

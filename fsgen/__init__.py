@@ -154,11 +154,12 @@ def batch_layout(seed: int, n_db: int = 512, lo: int = 1000, hi: int = 200_000,
 
 
 def make(name: str, seed: int = 0, workers: int = 1, n: int | None = None,
-         q: int | None = None, f: int | None = None) -> Workload:
+         q: int | None = None, f: int | None = None, n_db: int | None = None) -> Workload:
     """Build a named workload; ``n``/``q``/``f`` override the sizes (for
-    bounded samples of a large workload and for small test cases)."""
+    bounded samples of a large workload and for small test cases), ``n_db``
+    the number of databases of the batching workload (512)."""
     if name == "batching":
-        sizes, nq, ks = batch_layout(seed)
+        sizes, nq, ks = batch_layout(seed, n_db=n_db or 512)
         ff = f or 128
         seg_off = np.zeros(len(sizes) + 1, dtype=np.int64)
         np.cumsum(sizes, out=seg_off[1:])

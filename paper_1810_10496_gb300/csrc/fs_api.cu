@@ -170,6 +170,7 @@ struct StageTimer {
 
 struct Bounds {
     double scan, rq, rerank;
+    double rx;   // FP8 (per-row bounds): U, the bound on a unit vector's norm
 };
 
 Bounds score_bounds(const fs_db* db, double r_xmax) {
@@ -188,9 +189,21 @@ Bounds score_bounds(const fs_db* db, double r_xmax) {
     const double U = (1.0 + eta) * (1.0 + u);   // bound on ||u||
     Bounds b;
     b.rerank = gamma(m + 5) * U * U + e_norm;
+    b.rx = 0.0;
     if (db->prec == FS_FP32) {
         b.scan = (gamma(db->fu) * U * U + e_norm) * 1.25 + 1e-12;
         b.rq = 0.0;
+    } else if (db->prec == FS_FP8_E4M3) {
+        // FP8 with per-row bounds: for codes with residual norms r_q and r_x,
+        // |c_q.c_x - u_q.u_x| <= r_x (U + r_q) + U r_q (Cauchy-Schwarz, as
+        // below, with each row's own r_x). The row term is applied per row;
+        // here: the accumulation (8 K u sum|p|), the two scale products of
+        // the epilogue, the FP32 unit vectors, and 1e-6 for the FP32 rounding
+        // of the bounds themselves (values below 1.2, so far above it).
+        const double cmax = U * 1.1;
+        b.scan = 8.0 * db->fl * u * cmax * cmax + 6.0 * u * cmax * cmax + e_norm * 1.25 + 1e-6;
+        b.rq = U * 1.001;
+        b.rx = U;
     } else {
         // low-precision codes c with ||u - c|| = r: |c_q.c_x - u_q.u_x| <=
         // r_q (U + r_x) + U r_x by Cauchy-Schwarz. The residual norms are
@@ -222,11 +235,13 @@ struct Plan {
     int slots = 0;                  // resident scan blocks, or pairs of blocks
     bool pair = false;              // tensor-core scan on pairs of SMs
     int list_t = kListT;
+    int64_t total_band = 0;         // FP8: band-buffer entries
 };
 
 struct Layout {
-    size_t plan, q_order, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, counters, fb_list,
-        fb2_list, cand_fb, fb_score, fb_index, shared_thr, q_plan, total;
+    size_t plan, q_order, q_a64, q_ss, q_unit, q_lowp, q_scale, q_resid, cand, band, band_cnt,
+        class_thr, counters, fb_list, fb2_list, cand_fb, fb_score, fb_index, shared_thr, q_plan,
+        total;
 };
 
 bool tensor_scan(const fs_db* db) { return db->prec != FS_FP32; }
@@ -334,6 +349,17 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.chunk_rows = (int32_t)(chunk_tiles * pl.tile_rows);
         p.chunks = p.nrows > 0 ? (int32_t)ceil_div(p.nrows, p.chunk_rows) : 0;
         p.list_t = pl.list_t;
+        if (db->prec == FS_FP8_E4M3) {
+            // band capacity per query: the rows within the FP8 error of the k-th
+            // best (measured: a few hundred per million rows) plus the rows each
+            // list accepts before its running bound forms (many lists of one
+            // tile each, all in the first wave, are the worst case); never more
+            // rows than the segment has, so a segment of up to 8,192 rows
+            // cannot overflow
+            const int64_t want = std::min<int64_t>(65536, std::max<int64_t>(8192,
+                                                   round_up(ceil_div(p.nrows, 64), 256)));
+            p.band_cap = (int32_t)std::min<int64_t>(want, std::max<int64_t>(round_up(p.nrows, 32), 32));
+        }
         if (is_std_metric(db->metric)) {
             // the per-query bound is computed with the query (E = q_resid)
             p.bound_scan = 0.0f;
@@ -345,6 +371,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
             p.bound_scan = (float)b.scan;
             p.bound_rq = (float)b.rq;
             p.bound_rerank = (float)b.rerank;
+            p.bound_rx = (float)b.rx;
         }
         if (p.nq > 0 && p.nrows > 0) seg_work[s] = (int64_t)p.units * row_tiles;
     }
@@ -356,14 +383,20 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
                      [&](int32_t a, int32_t b) { return seg_work[a] > seg_work[b]; });
     std::vector<SegPlan> sorted(n_seg);
     std::vector<int32_t> pos_of(n_seg);
-    int64_t item = 0, cand = 0;
+    int64_t item = 0, cand = 0, band = 0;
+    const bool fp8 = db->prec == FS_FP8_E4M3 && !is_std_metric(db->metric);
     for (int i = 0; i < n_seg; ++i) {
         SegPlan p = pl.seg[order[i]];
         p.item0 = item;
         p.cand0 = cand;
+        p.band0 = band;
         if (p.nq > 0 && p.nrows > 0) {
             item += (int64_t)p.units * p.chunks;
-            cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
+            // the FP8 scan keeps a band per query instead of candidate lists
+            if (fp8)
+                band += (int64_t)p.nq * p.band_cap;
+            else
+                cand += (int64_t)p.nq * p.chunks * p.lists * pl.list_t;
         }
         sorted[i] = p;
         pos_of[order[i]] = i;
@@ -374,6 +407,7 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
     for (int s = 0; s < n_seg; ++s) pl.q_order[s] = pos_of[s];
     pl.total_items = item;
     pl.total_cand = cand;
+    pl.total_band = band;
     return FS_OK;
 }
 
@@ -395,6 +429,9 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.q_scale = take(sizeof(float) * nq);
     L.q_resid = take(sizeof(float) * nq);
     L.cand = take(sizeof(uint64_t) * (size_t)pl.total_cand);
+    L.band = take(sizeof(uint64_t) * (size_t)pl.total_band);
+    L.band_cnt = take(sizeof(int32_t) * (db->prec == FS_FP8_E4M3 ? nq : 0));
+    L.class_thr = take(sizeof(uint32_t) * (db->prec == FS_FP8_E4M3 ? (size_t)nq * FS_MAX_K : 0));
     L.counters = take(4 * sizeof(int32_t));
     L.fb_list = take(sizeof(int32_t) * nq);
     L.fb2_list = take(sizeof(int32_t) * nq);
@@ -478,6 +515,9 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.q_scale = (float*)(ws + L.q_scale);
     c.q_resid = (float*)(ws + L.q_resid);
     c.cand = (uint64_t*)(ws + L.cand);
+    c.band = (uint64_t*)(ws + L.band);
+    c.band_cnt = (int32_t*)(ws + L.band_cnt);
+    c.class_thr = (uint32_t*)(ws + L.class_thr);
     c.fb_count = (int32_t*)(ws + L.counters);
     c.work_counter = c.fb_count + 1;
     c.fb2_count = c.fb_count + 2;
@@ -513,6 +553,10 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
                                         db->fl, c.q_scale, c.q_resid, db->prec, db->status, cs));
         // 0 sorts below every order-mapped score
         FS_CUDA(cudaMemsetAsync(c.shared_thr, 0, sizeof(uint32_t) * nq, cs));
+        if (db->prec == FS_FP8_E4M3) {
+            FS_CUDA(cudaMemsetAsync(c.band_cnt, 0, sizeof(int32_t) * nq, cs));
+            FS_CUDA(cudaMemsetAsync(c.class_thr, 0, sizeof(uint32_t) * nq * FS_MAX_K, cs));
+        }
         t.finish((int)ceil_div(db->n_seg, 256) + 2);
     }
     if (pl.total_items > 0) {

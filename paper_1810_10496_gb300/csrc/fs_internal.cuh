@@ -149,8 +149,12 @@ struct SegPlan {
     int32_t seg;         // index of the segment in the database
     float mag_max;       // standardised metrics: the segment's largest row magnitude
                          // (Euclidean |z|, Manhattan sum |z_i|), for the score bound
+    int64_t band0;       // FP8: first band-buffer entry of the segment
+    int32_t band_cap;    // FP8: band-buffer entries per query
+    float bound_rx;      // FP8: per-row bound E = a + (bound_rx + r_q) * 1.001 * r_x,
+                         //   a = bound_scan + bound_rq * r_q (r: residual norms)
 };
-static_assert(sizeof(SegPlan) == 88, "SegPlan layout");
+static_assert(sizeof(SegPlan) == 104, "SegPlan layout");
 
 // Read-only device view of a database and of one call's workspace.
 struct DbView {
@@ -186,7 +190,11 @@ struct CallView {
     void* q_lowp;             // [nq][fl]
     float* q_scale;           // [nq]
     float* q_resid;           // [nq]
-    uint64_t* cand;           // candidate lists
+    uint64_t* cand;           // candidate lists (BF16 / FP32 scans)
+    uint64_t* band;           // FP8 scan: per query, the keys of every row whose score's
+                              // upper bound reached the running k-th best lower bound
+    int32_t* band_cnt;        // [nq] rows appended to each query's band (may exceed the
+                              // capacity: then the query goes to the exact fallback)
     int32_t* fb_count;        // queries sent to the FP32 rescan (fb_count[1] is the
                               // scan scheduler, fb_count[2] is fb2_count, fb_count[3]
                               // is `aborted`)
@@ -204,6 +212,8 @@ struct CallView {
     int32_t withhold_load;    // test aid: every scan block skips its first row-tile load
     uint32_t* shared_thr;     // [nq] per query: a score below which no row can be
                               // among the k nearest (order-mapped bits)
+    uint32_t* class_thr;      // FP8: [nq][FS_MAX_K] per query and row class (row mod k):
+                              // the best lower bound of a band row of the class
     const int32_t* exclude;   // [nq] or NULL
     int32_t* out_idx;         // [nq][k_max]
     float* out_dist;          // [nq][k_max]

@@ -69,9 +69,6 @@ struct Bars {
     uint64_t a_full;
     uint64_t a_empty;
     uint64_t drain;
-    uint64_t sx_ready[kAccs];   // FP8: the tile's row scales are staged
-    uint64_t pfull[kMaxStages]; // pairs (leader): the odd CTA's ring slot landed
-    uint64_t pa_full;           // pairs (leader): the odd CTA's query tile landed
     uint64_t item_full[kItemQ]; // a claimed item (or the end, -1) is in item_q
     uint64_t item_empty[kItemQ];// the MMA thread and every epilogue warp have read it
 };
@@ -142,13 +139,23 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64
         if (globaltimer() - t0 > wlim) break;
 }
 
+// A spin of about `ns` nanoseconds (the pair path's grace period for its own
+// copies on the way out, see below).
+__device__ __forceinline__ void spin_ns(uint64_t ns) {
+    const uint64_t t0 = globaltimer();
+    while (globaltimer() - t0 < ns) {
+    }
+}
+
 // PAIR: a cluster of two CTAs shares every tile (cta_group::2). Each CTA
-// loads its own 128 queries and its own half (128 rows) of each tile's rows;
-// the even CTA ("leader") issues M = 256 MMAs over both, and each CTA's
-// tensor memory receives its queries' 128 x 256 scores. The odd CTA's warp 1
-// forwards the completion of its loads to the leader's barriers; the
-// leader's commits reach the barriers of both CTAs; the odd CTA's epilogue
-// frees an accumulator with an arrival on the leader's barrier.
+// loads its own 128 queries and its own half (128 rows) of each tile's rows
+// into its own shared memory, and both CTAs' copies signal the barriers of
+// the even CTA ("leader"), which expects the bytes of both; the leader issues
+// M = 256 MMAs over both, and each CTA's tensor memory receives its queries'
+// 128 x 256 scores. The leader's commits reach the barriers of both CTAs (a
+// CTA refills a ring slot once its own copy of the commit arrives); the odd
+// CTA's epilogue frees an accumulator with an arrival on the leader's
+// barrier.
 template <bool FP8, int LT, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
@@ -158,7 +165,12 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
     __shared__ int32_t item_q[kItemQ];
-    __shared__ __align__(16) float sx[kAccs][BN];   // FP8: the tile's row scales, per accumulator
+    // FP8: per epilogue warp, the row scales and residual norms of its half of
+    // the current tile, and per group of 8 rows the largest residual (each
+    // warp stages its own copy: no barrier across warps)
+    __shared__ __align__(16) float wsx[kEpiWarps][BN / 2];
+    __shared__ __align__(16) float wrx[kEpiWarps][BN / 2];
+    __shared__ float wgrx[kEpiWarps][BN / 16];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -180,9 +192,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_u32(&bars.full[s]), 1);
             mbar_init(smem_u32(&bars.empty[s]), 1);
-            mbar_init(smem_u32(&bars.pfull[s]), 1);
         }
-        mbar_init(smem_u32(&bars.pa_full), 1);
         for (int a = 0; a < kAccs; ++a) {
             mbar_init(smem_u32(&bars.tmem_full[a]), 1);
             mbar_init(smem_u32(&bars.tmem_empty[a]), (PAIR ? 2 : 1) * kEpiWarps);
@@ -194,7 +204,6 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             mbar_init(smem_u32(&bars.item_full[i]), 1);
             mbar_init(smem_u32(&bars.item_empty[i]), 1 + kEpiWarps);
         }
-        for (int a = 0; a < kAccs; ++a) mbar_init(smem_u32(&bars.sx_ready[a]), kEpiThreads);
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -215,6 +224,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
         if (lane == 0) {
             prefetch_tensormap(&map_q);
             prefetch_tensormap(&map_x);
+            // pairs: the leader's query-tile and ring barriers (cluster addresses)
+            const uint32_t lead_a_full = PAIR ? mapa_shared(smem_u32(&bars.a_full), 0) : 0u;
+            const uint32_t lead_full0 = PAIR ? mapa_shared(smem_u32(&bars.full[0]), 0) : 0u;
+            (void)lead_a_full;
+            (void)lead_full0;
             uint32_t it = 0, ic = 0, a_loads = 0;
             bool ok = true;
             for (uint32_t n = 0; ok; ++n, ++ic) {
@@ -228,10 +242,19 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_empty), (ic & 1) ^ 1, &abort_flag, wlim);
                 if (!ok) break;
-                mbar_arrive_expect_tx(smem_u32(&bars.a_full), kblocks * kABlockBytes);
-                for (int kb = 0; kb < kblocks; ++kb)
-                    tma_load_2d(a_smem + kb * kABlockBytes, &map_q, smem_u32(&bars.a_full),
-                                kb * kElemsPerKBlock, w.qbase);
+                if (PAIR) {
+                    // the leader's barrier counts the query tiles of both CTAs
+                    if (leader)
+                        mbar_arrive_expect_tx(smem_u32(&bars.a_full), 2 * kblocks * kABlockBytes);
+                    for (int kb = 0; kb < kblocks; ++kb)
+                        tma_load_2d_pair(a_smem + kb * kABlockBytes, &map_q, lead_a_full,
+                                         kb * kElemsPerKBlock, w.qbase);
+                } else {
+                    mbar_arrive_expect_tx(smem_u32(&bars.a_full), kblocks * kABlockBytes);
+                    for (int kb = 0; kb < kblocks; ++kb)
+                        tma_load_2d(a_smem + kb * kABlockBytes, &map_q, smem_u32(&bars.a_full),
+                                    kb * kElemsPerKBlock, w.qbase);
+                }
                 ++a_loads;
                 for (int t = 0; ok && t < w.ntiles; ++t) {
                     // this CTA's rows of the tile: all 256, or its half of them
@@ -244,13 +267,26 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         // test aid: the first ring slot is never filled, so the MMA
                         // issuer's wait for it runs out (nothing is left in flight)
                         if (call.withhold_load && it == 0) continue;
-                        mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kBStage);
-                        tma_load_2d(b_smem + s * kBStage, &map_x, smem_u32(&bars.full[s]),
-                                    kb * kElemsPerKBlock, row);
+                        if (PAIR) {
+                            if (leader) mbar_arrive_expect_tx(smem_u32(&bars.full[s]), 2 * kBStage);
+                            tma_load_2d_pair(b_smem + s * kBStage, &map_x,
+                                             lead_full0 + s * (uint32_t)sizeof(uint64_t),
+                                             kb * kElemsPerKBlock, row);
+                        } else {
+                            mbar_arrive_expect_tx(smem_u32(&bars.full[s]), kBStage);
+                            tma_load_2d(b_smem + s * kBStage, &map_x, smem_u32(&bars.full[s]),
+                                        kb * kElemsPerKBlock, row);
+                        }
                     }
                 }
             }
-            if (!ok) {
+            if (!ok && PAIR) {
+                // A pair's copies signal the leader's barriers, which the odd CTA
+                // cannot wait on: both CTAs leave their copies in flight a grace
+                // period to land (a tile copy takes microseconds; the wait that
+                // gave up took far longer).
+                spin_ns(200000);
+            } else if (!ok) {
                 // let the copies already issued land before the block exits (the
                 // withheld slot, if any, has nothing to wait for)
                 for (uint32_t j = (it >= (uint32_t)stages ? it - stages : 0); j < it; ++j)
@@ -282,7 +318,6 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 }
                 const Item w = decode(call, item, rank, PAIR);
                 ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag, wlim);
-                if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pa_full), ic & 1, &abort_flag, wlim);
                 if (!ok) break;
                 tc_fence_after();
                 for (int t = 0; ok && t < w.ntiles; ++t, ++tcount) {
@@ -294,7 +329,6 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     for (int kb = 0; kb < kblocks; ++kb, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1;
                         ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag, wlim);
-                        if (ok && PAIR) ok = mbar_wait(smem_u32(&bars.pfull[s]), ph, &abort_flag, wlim);
                         if (!ok) break;
                         tc_fence_after();
 #pragma unroll
@@ -325,36 +359,15 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             drain_wait(smem_u32(&bars.drain), 0, wlim);
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ load forwarder
-        // (odd CTA of a pair) its query tile and ring slots landing, passed on
-        // to the leader's barriers in the order the leader consumes them
-        if (lane == 0) {
-            const uint32_t r_pa_full = mapa_shared(smem_u32(&bars.pa_full), 0);
-            uint32_t it = 0, ic = 0;
-            bool ok = true;
-            for (int64_t item = unit0; ok && item < call.total_items; item += nunits, ++ic) {
-                const Item w = decode(call, item, rank, PAIR);
-                ok = mbar_wait(smem_u32(&bars.a_full), ic & 1, &abort_flag, wlim);
-                if (!ok) break;
-                mbar_arrive_cluster(r_pa_full);
-                for (int t = 0; ok && t < w.ntiles; ++t) {
-                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
-                        const uint32_t s = it % stages, ph = (it / stages) & 1;
-                        ok = mbar_wait(smem_u32(&bars.full[s]), ph, &abort_flag, wlim);
-                        if (!ok) break;
-                        mbar_arrive_cluster(mapa_shared(smem_u32(&bars.pfull[s]), 0));
-                    }
-                }
-            }
-            // the leader's last commit: every MMA writing this CTA's TMEM is done
-            drain_wait(smem_u32(&bars.drain), 0, wlim);
-        }
+        // ------------------------------------------------ odd CTA of a pair
+        // the leader's last commit: every MMA writing this CTA's TMEM is done
+        if (lane == 0) drain_wait(smem_u32(&bars.drain), 0, wlim);
     } else {
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;              // TMEM lanes this warp may read
         const int lq = quarter * 32 + lane;        // query row of the tile
-        const int et = threadIdx.x - 64;           // epilogue thread 0..255
         const int half = (warp - 2) >> 2;          // which half of each tile's columns
+        const int ew = warp - 2;                   // epilogue warp 0..7
         constexpr int kHalfCols = BN / 2;
         uint32_t tcount = 0;
         bool ok = true;
@@ -380,61 +393,121 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             const bool qvalid = lq < w.nq_tile && call.q_ss[w.qbase + lq] != 0.0f;
             const int excl = (call.exclude && qvalid) ? call.exclude[w.qbase + lq] : -1;
             const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
+            const float rq = qvalid ? call.q_resid[w.qbase + lq] : 0.0f;
+            // BF16: the list of the LT best (score, row) pairs. FP8: the LT best
+            // lower bounds g = s - b r_x of the rows seen (rows unused).
             RegList<LT> st;
             st.reset();
 
             float published = -INFINITY;
-            // Pruning bound shared by every block scanning this query: the k-th
-            // best approximate score any block has seen, minus twice the score
-            // error bound E. A row scoring below it is at least 2E under k rows'
-            // scores, so its cosine is below theirs: it cannot be among the k
-            // nearest, and dropping it never affects certification. Read one
-            // tile ahead so the L2 round trip overlaps the current tile.
-            const float e2 =
-                qvalid ? 2.0f * (w.p.bound_scan + w.p.bound_rq * call.q_resid[w.qbase + lq]) * 1.0001f
-                       : 0.0f;
-            const uint32_t* shared_p = call.shared_thr + w.qbase + lq;
-            uint32_t shared_next = qvalid ? __ldcg(shared_p) : 0xffffffffu;
+            // Pruning bound shared by every block scanning this query. BF16: the
+            // k-th best approximate score any block has seen, minus twice the
+            // score error bound E; a row scoring below it is at least 2E under k
+            // rows' scores, so its cosine is below theirs: it cannot be among the
+            // k nearest, and dropping it never affects certification. FP8: the
+            // k-th best lower bound s - E_x any block has seen (E_x the row's own
+            // bound); a row whose upper bound s + E_x is below it cannot be among
+            // the k nearest. Read one tile ahead so the L2 round trip overlaps
+            // the current tile.
+            const float e2 = qvalid ? 2.0f * (w.p.bound_scan + w.p.bound_rq * rq) * 1.0001f : 0.0f;
+            // FP8 per-row bound E_x = fa + fb r_x, each coefficient a little above
+            // the selection's binary64 one (a = bound_scan + bound_rq r_q,
+            // b = 1.001 (bound_rx + r_q)), so FP32 rounding here never drops a row
+            // the selection's test would keep
+            const float fa = (w.p.bound_scan + w.p.bound_rq * rq) * 1.0001f;
+            const float fb = (w.p.bound_rx + rq) * 1.0011f;
+            // FP8: the shared bound is the least of k class slots (rows of class
+            // c = local row mod k): each slot holds the best lower bound of a
+            // band row of its class, so k distinct band rows reach the least of
+            // them (0 = a class without one yet: no bound)
+            const uint32_t* shared_p =
+                FP8 ? call.class_thr + (int64_t)(w.qbase + lq) * FS_MAX_K : call.shared_thr + w.qbase + lq;
+            auto read_shared = [&]() -> uint32_t {
+                if (!FP8) return __ldcg(shared_p);
+                uint32_t mn = 0xffffffffu;
+                for (int c = 0; c < w.p.k; ++c) mn = min(mn, __ldcg(shared_p + c));
+                return mn;
+            };
+            uint32_t shared_next = qvalid ? read_shared() : 0xffffffffu;
+            // FP8: per class, the best lower bound g of this list's band rows,
+            // and which classes improved since the last publication
+            float cbest[LT];
+#pragma unroll
+            for (int c = 0; c < LT; ++c) cbest[c] = -INFINITY;
+            uint32_t cdirty = 0;
+            // FP8: this query's band (rows whose upper bound reaches the running
+            // k-th best lower bound), appended through its counter
+            uint64_t* band = nullptr;
+            int32_t* band_cnt = nullptr;
+            if (FP8 && qvalid) {
+                band = call.band + w.p.band0 + ((int64_t)w.qtile * BM + lq) * w.p.band_cap;
+                band_cnt = call.band_cnt + w.qbase + lq;
+            }
             for (int t = 0; t < w.ntiles; ++t, ++tcount) {
                 const uint32_t acc = tcount % kAccs, aph = (tcount / kAccs) & 1;
                 const int64_t tile_row0 = w.row_begin + (int64_t)t * BN;
                 const float shared_s = qvalid ? unord_f32(shared_next) : INFINITY;
-                if (qvalid && t + 1 < w.ntiles) shared_next = __ldcg(shared_p);
+                if (qvalid && t + 1 < w.ntiles) shared_next = read_shared();
+                // FP8: the scales and residual norms of this warp's half of the
+                // tile, loaded before the wait for the accumulator (lane l: the
+                // half's columns l, l + 32, l + 64, l + 96; rows past the data: 0)
+                float pre_s[4], pre_r[4];
                 if (FP8) {
-                    // stage the tile's row scales (rows past the data read as 0); every
-                    // epilogue thread finished tile t-kAccs, the last user of sx[acc],
-                    // before any thread could complete the phase of the tile after it
-                    for (int j = et; j < BN; j += kEpiThreads) {
-                        const int64_t r = tile_row0 + j;
-                        sx[acc][j] = r < w.row_end ? db.scale[r] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int64_t r = tile_row0 + half * kHalfCols + 32 * i + lane;
+                        const bool in = r < w.row_end;
+                        pre_s[i] = in ? db.scale[r] : 0.0f;
+                        pre_r[i] = in ? db.resid[r] : 0.0f;
                     }
-                    mbar_arrive(smem_u32(&bars.sx_ready[acc]));
-                    ok = mbar_wait(smem_u32(&bars.sx_ready[acc]), aph, &abort_flag, wlim);
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
                 }
                 ok = mbar_wait(smem_u32(&bars.tmem_full[acc]), aph, &abort_flag, wlim);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
+                if (FP8) {
+                    // staged for this warp alone (its previous tile is done: every
+                    // lane passed the __syncwarp at its end)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        wsx[ew][32 * i + lane] = pre_s[i];
+                        wrx[ew][32 * i + lane] = pre_r[i];
+                        float rmax = pre_r[i];
+#pragma unroll
+                        for (int o = 1; o < 8; o <<= 1)
+                            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                        if ((lane & 7) == 0) wgrx[ew][4 * i + (lane >> 3)] = rmax;
+                    }
+                    __syncwarp();
+                }
                 const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
                 bool offered = false;   // the list may have changed in this tile
+                // FP8 threshold on h = s + fb r_x (the upper bound minus fa)
+                const float shared_h = shared_s - fa;
 #pragma unroll 1
                 for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 64) {
                     uint32_t r0[32], r1[32];
                     tmem_ld_32x32b_x32(taddr + c0, r0);
                     tmem_ld_32x32b_x32(taddr + c0 + 32, r1);
                     tmem_ld_wait();
-                    // FP8: w = acc * s_row here, the query scale follows (a positive
-                    // factor: the maxima below stay maxima after scaling)
+                    // FP8: v = acc * s_row (the codes are unit elements divided by
+                    // their row's scale, so the row scale belongs to each score before
+                    // any maximum); BF16: v = acc
                     float v[64];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         v[j] = __uint_as_float(r0[j]);
                         v[32 + j] = __uint_as_float(r1[j]);
-                        if (FP8) {
-                            v[j] *= sx[acc][c0 + j];
-                            v[32 + j] *= sx[acc][c0 + 32 + j];
+                    }
+                    if (FP8) {
+                        const float4* s4 = reinterpret_cast<const float4*>(&wsx[ew][c0 - half * kHalfCols]);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float4 sc4 = s4[j];
+                            v[4 * j] *= sc4.x;
+                            v[4 * j + 1] *= sc4.y;
+                            v[4 * j + 2] *= sc4.z;
+                            v[4 * j + 3] *= sc4.w;
                         }
                     }
                     float gm[8];
@@ -443,42 +516,120 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         const float a = fmax3(v[8 * g], v[8 * g + 1], v[8 * g + 2]);
                         const float b = fmax3(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]);
                         const float mx = fmax3(a, b, fmaxf(v[8 * g + 6], v[8 * g + 7]));
-                        gm[g] = FP8 ? mx * sq : mx;
+                        if (FP8) {
+                            // an upper bound on h over the group: its largest scaled
+                            // score times the query scale (a non-negative factor), plus
+                            // fb times the group's largest residual; each step rounds
+                            // monotonically, so no h of the group exceeds it
+                            const int gi = ((c0 - half * kHalfCols) >> 3) + g;
+                            gm[g] = fmaf(fb, wgrx[ew][gi], mx * sq);
+                        } else {
+                            gm[g] = mx;
+                        }
                     }
                     const float m = fmax3(fmax3(gm[0], gm[1], gm[2]), fmax3(gm[3], gm[4], gm[5]),
                                           fmaxf(gm[6], gm[7]));
-                    float thr = fmaxf(st.thr_s, shared_s);
-                    if (__any_sync(0xffffffffu, m >= thr)) {
-                        // group by group, with the threshold as it stands (a list that
-                        // is filling tightens after every group): each lane collects
-                        // its passing columns of the group, then every lane takes its
-                        // next candidate in the same round
+                    if (FP8) {
+                        float thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa : -INFINITY,
+                                          shared_h);
+                        if (__any_sync(0xffffffffu, m >= thr)) {
+                            // Group by group (a loop kept rolled: the group's 8 scores
+                            // are rotated to the front of v, so the body is compiled
+                            // once and stays in the instruction cache):
+                            // 1: the rows' lower bounds g = s - fb r_x join the list of
+                            //    the LT best (a row's g is at most its h, so a group
+                            //    whose bound on h is under thr holds no g the list
+                            //    keeps), and the threshold tightens;
+                            // 2: the rows whose h = s + fb r_x reaches it are appended
+                            //    to the band (the list's own k best are among them:
+                            //    their h is at least their g).
+#pragma unroll 1
+                            for (int g = 0; g < 8; ++g) {
+                                if (__any_sync(0xffffffffu, gm[0] >= thr)) {
+                                    const int lcg = c0 + 8 * g - half * kHalfCols;   // in the half
+                                    const int64_t row0g = tile_row0 + c0 + 8 * g;
+                                    if (gm[0] >= thr) {
 #pragma unroll
-                        for (int g = 0; g < 8; ++g) {
-                            if (__any_sync(0xffffffffu, gm[g] >= thr)) {
-                                uint32_t bits = 0;
+                                        for (int i = 0; i < 8; ++i) {
+                                            const int64_t row = row0g + i;
+                                            if (row < w.row_end && (int)(row - w.p.row0) != excl)
+                                                st.offer(fmaf(-fb, wrx[ew][lcg + i], v[i] * sq), 0, 1, 0, -1);
+                                        }
+                                    }
+                                    thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa
+                                                                : -INFINITY,
+                                                shared_h);
+                                    uint32_t bits = 0;
 #pragma unroll
-                                for (int i = 0; i < 8; ++i) {
-                                    const float sc = FP8 ? v[8 * g + i] * sq : v[8 * g + i];
-                                    bits |= (sc >= thr ? 1u : 0u) << i;
-                                }
-                                while (__any_sync(0xffffffffu, bits != 0)) {
+                                    for (int i = 0; i < 8; ++i) {
+                                        const float h = fmaf(fb, wrx[ew][lcg + i], v[i] * sq);
+                                        const int64_t row = row0g + i;
+                                        const bool in = h >= thr && row < w.row_end &&
+                                                        (int)(row - w.p.row0) != excl;
+                                        bits |= (in ? 1u : 0u) << i;
+                                    }
                                     if (bits != 0) {
-                                        const int i = __ffs(bits) - 1;
-                                        bits &= bits - 1;
-                                        const float a0 = (i & 1) ? v[8 * g + 1] : v[8 * g];
-                                        const float a1 = (i & 1) ? v[8 * g + 3] : v[8 * g + 2];
-                                        const float a2 = (i & 1) ? v[8 * g + 5] : v[8 * g + 4];
-                                        const float a3 = (i & 1) ? v[8 * g + 7] : v[8 * g + 6];
-                                        const float b0 = (i & 2) ? a1 : a0;
-                                        const float b1 = (i & 2) ? a3 : a2;
-                                        const float raw = (i & 4) ? b1 : b0;
-                                        const float sc = FP8 ? raw * sq : raw;
-                                        if (sc >= thr) {
-                                            st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
-                                                     w.p.row0, excl);
-                                            thr = fmaxf(st.thr_s, shared_s);
-                                            offered = true;
+                                        int at = atomicAdd(band_cnt, __popc(bits));
+                                        for (uint32_t b = bits; b != 0; b &= b - 1, ++at) {
+                                            const int i = __ffs(b) - 1;
+                                            // v[i] without a run-time register index
+                                            float vi = v[0];
+#pragma unroll
+                                            for (int i2 = 1; i2 < 8; ++i2)
+                                                if (i2 == i) vi = v[i2];
+                                            const float sc = vi * sq;
+                                            const uint32_t li = (uint32_t)(row0g + i - w.p.row0);
+                                            if (at < w.p.band_cap) band[at] = make_key(sc, li);
+                                            // the best lower bound of its class
+                                            const int cls = (int)(li % (uint32_t)w.p.k);
+                                            const float gl = fmaf(-fb, wrx[ew][lcg + i], sc);
+#pragma unroll
+                                            for (int c = 0; c < LT; ++c)
+                                                if (c == cls && gl > cbest[c]) {
+                                                    cbest[c] = gl;
+                                                    cdirty |= 1u << c;
+                                                }
+                                        }
+                                    }
+                                }
+                                // the next group to the front
+#pragma unroll
+                                for (int j = 0; j < 56; ++j) v[j] = v[j + 8];
+#pragma unroll
+                                for (int j = 0; j < 7; ++j) gm[j] = gm[j + 1];
+                            }
+                        }
+                    } else {
+                        float thr = fmaxf(st.thr_s, shared_s);
+                        if (__any_sync(0xffffffffu, m >= thr)) {
+                            // group by group, with the threshold as it stands (a list
+                            // that is filling tightens after every group): each lane
+                            // collects its passing columns of the group, then every
+                            // lane takes its next candidate in the same round
+#pragma unroll
+                            for (int g = 0; g < 8; ++g) {
+                                if (__any_sync(0xffffffffu, gm[g] >= thr)) {
+                                    uint32_t bits = 0;
+#pragma unroll
+                                    for (int i = 0; i < 8; ++i)
+                                        bits |= (v[8 * g + i] >= thr ? 1u : 0u) << i;
+                                    while (__any_sync(0xffffffffu, bits != 0)) {
+                                        if (bits != 0) {
+                                            const int i = __ffs(bits) - 1;
+                                            bits &= bits - 1;
+                                            const float a0 = (i & 1) ? v[8 * g + 1] : v[8 * g];
+                                            const float a1 = (i & 1) ? v[8 * g + 3] : v[8 * g + 2];
+                                            const float a2 = (i & 1) ? v[8 * g + 5] : v[8 * g + 4];
+                                            const float a3 = (i & 1) ? v[8 * g + 7] : v[8 * g + 6];
+                                            const float b0 = (i & 2) ? a1 : a0;
+                                            const float b1 = (i & 2) ? a3 : a2;
+                                            const float sc = (i & 4) ? b1 : b0;
+                                            if (sc >= thr) {
+                                                st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
+                                                         w.p.row0, excl);
+                                                thr = fmaxf(st.thr_s, shared_s);
+                                                offered = true;
+                                            }
                                         }
                                     }
                                 }
@@ -496,7 +647,18 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     else
                         mbar_arrive(bar);
                 }
-                if (qvalid && offered && st.cnt >= w.p.k) {
+                if (FP8) {
+                    // the class slots that improved: g - fa, rounded down (the bound
+                    // may only err low)
+                    if (qvalid && cdirty != 0) {
+#pragma unroll
+                        for (int c = 0; c < LT; ++c)
+                            if ((cdirty >> c) & 1u)
+                                atomicMax(call.class_thr + (int64_t)(w.qbase + lq) * FS_MAX_K + c,
+                                          ord_f32((cbest[c] - fa) - fabsf(cbest[c]) * 0x1p-20f));
+                    }
+                    cdirty = 0;
+                } else if (qvalid && offered && st.cnt >= w.p.k) {
                     const float kth = st.kth_score(w.p.k);
                     // rounded down: the bound may only err low
                     const float bound = (kth - e2) - fabsf(kth) * 0x1p-20f;
@@ -506,7 +668,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     }
                 }
             }
-            if (ok && qvalid) {
+            if (!FP8 && ok && qvalid) {
                 const int64_t qlocal = (int64_t)w.qtile * BM + lq;
                 uint64_t* dst = call.cand + w.p.cand0 +
                                 ((qlocal * w.p.chunks + w.chunk) * 2 + half) * (int64_t)LT;
@@ -563,7 +725,8 @@ int scan_tc_stages(int kblocks, bool fp8, bool pair) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 232448;
-    const size_t static_bytes = sizeof(Bars) + 64 + (fp8 ? kAccs * BN * sizeof(float) : 0);
+    const size_t static_bytes =
+        sizeof(Bars) + 64 + (fp8 ? (2 * kEpiWarps * (BN / 2) + kEpiWarps * (BN / 16)) * sizeof(float) : 0);
     const long avail = (long)optin - (long)static_bytes - 1024 - (long)kblocks * kABlockBytes;
     int st = (int)(avail / (long)(pair ? kStageBytes / 2 : kStageBytes));
     return st < 2 ? 2 : (st > kMaxStages ? kMaxStages : st);

@@ -175,6 +175,45 @@ __device__ double exact_norm2(const float* __restrict__ q, int f) {
     return a;
 }
 
+// FP32 rescoring of kRescoreRows rows (row < 0: none) against the query's
+// unit vector: the cosine u_q . u_x as a warp-wide sum (each lane sums the
+// features lane, lane + 32, ... with FMA, then a butterfly; every lane ends
+// with the same bits), and with DIST also 1/2 |u_q - u_x|^2 the same way. The
+// error of the cosine is within the plan's bound_rerank.
+template <bool DIST>
+__device__ __forceinline__ void rescore_rows(const DbView& db, const float* __restrict__ qu,
+                                             const int64_t (&row)[kRescoreRows],
+                                             float (&dot)[kRescoreRows],
+                                             float (&dd)[kRescoreRows], int lane) {
+#pragma unroll
+    for (int j = 0; j < kRescoreRows; ++j) {
+        dot[j] = 0.0f;
+        dd[j] = 0.0f;
+        if (row[j] >= 0) {
+            const float* xu = db.unit + row[j] * (int64_t)db.fu;
+            for (int i = lane; i < db.fu; i += 32) {
+                const float a = qu[i], b = xu[i];
+                dot[j] = fmaf(a, b, dot[j]);
+                if (DIST) {
+                    const float t = a - b;
+                    dd[j] = fmaf(t, t, dd[j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kRescoreRows; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dot[j] += __shfl_xor_sync(kFull, dot[j], o);
+            if (DIST) dd[j] += __shfl_xor_sync(kFull, dd[j], o);
+        }
+    }
+}
+
+__device__ int finish_window(const DbView& db, const CallView& call, SelShared& sh, int wid,
+                             int lane, int q, const SegPlan& p, int nw, unsigned long long* stats);
+
 // Answers query q from its candidate lists: cand holds nl lists of lt keys
 // (each sorted, descending, empty entries last),
 // every approximate score within E of the exact cosine. Returns the number of
@@ -276,6 +315,16 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
         return nw < k ? nw : k;
     }
 
+    return finish_window(db, call, sh, wid, lane, q, p, nw, stats);
+}
+
+// Steps 4-8 for a certified window of nw <= kWindow candidates in sh.widx:
+// every row that can be among the k nearest is in it. Returns the number of
+// places written. Whole warp.
+__device__ int finish_window(const DbView& db, const CallView& call, SelShared& sh, int wid,
+                             int lane, int q, const SegPlan& p, int nw, unsigned long long* stats) {
+    const int k = p.k;
+    const int64_t out0 = (int64_t)q * call.k_max;
     // 4. FP32 rescoring of the window: the cosine of the unit vectors and
     //    the distance 1/2 |u_q - u_x|^2 (no cancellation near 0)
     //    (kRescoreRows window rows per pass, so their loads overlap)
@@ -284,27 +333,11 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
         float dot[kRescoreRows], dd[kRescoreRows];
         int64_t row[kRescoreRows];
 #pragma unroll
-        for (int j = 0; j < kRescoreRows; ++j) {
-            dot[j] = 0.0f;
-            dd[j] = 0.0f;
+        for (int j = 0; j < kRescoreRows; ++j)
             row[j] = w0 + j < nw ? p.row0 + sh.widx[wid][w0 + j] : -1;
-            if (row[j] >= 0) {
-                const float* xu = db.unit + row[j] * (int64_t)db.fu;
-                for (int i = lane; i < db.fu; i += 32) {
-                    const float a = qu[i], b = xu[i];
-                    dot[j] = fmaf(a, b, dot[j]);
-                    const float t = a - b;
-                    dd[j] = fmaf(t, t, dd[j]);
-                }
-            }
-        }
+        rescore_rows<true>(db, qu, row, dot, dd, lane);
 #pragma unroll
         for (int j = 0; j < kRescoreRows; ++j) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                dot[j] += __shfl_xor_sync(kFull, dot[j], o);
-                dd[j] += __shfl_xor_sync(kFull, dd[j], o);
-            }
             if (lane == 0 && row[j] >= 0) {
                 sh.wsc[wid][w0 + j] = dot[j];
                 // a zero row has cosine 0 by convention: d = 1
@@ -422,8 +455,125 @@ __device__ int answer_from_lists(const DbView& db, const CallView& call, SelShar
     return nout;
 }
 
-// (at most 48 registers: five blocks per SM, fewer waves on large batches)
-__global__ void __launch_bounds__(kSelWarps * 32, 5)
+// Answers query q from its FP8 band: the keys (approximate score s, row) of
+// every row whose upper bound s + E_x reached the scan's running k-th best
+// lower bound, E_x = a + b r_x the row's own bound (r_x its residual norm; a
+// and b per query, from the plan). Returns the places written, or -1 when the
+// band does not certify the answer (it overflowed its buffer, or more than
+// kWindow rows lie within the FP32 rescoring's error of the k-th). Whole warp.
+//
+//  A. L = the k-th best lower bound s - E_x over the band: k rows have cosine
+//     at least L, so no row with s + E_x < L is among the k nearest. The band
+//     holds every row with s + E_x >= L (the scan's running bound was never
+//     above L), the k nearest among them.
+//  B. Every band row with s + E_x >= L is rescored in FP32 (error E_r); the
+//     others are cleared.
+//  C. t = the k-th best FP32 score; the rows within 2 E_r of it form the
+//     window of steps 4-8, which contains the k nearest.
+__device__ int answer_from_band(const DbView& db, const CallView& call, SelShared& sh, int wid,
+                                int lane, int q, const SegPlan& p, unsigned long long* stats) {
+    const int k = p.k;
+    const int n = call.band_cnt[q];
+    if (n > p.band_cap) return -1;   // the band overflowed its buffer
+    uint64_t* band = call.band + p.band0 + (int64_t)(q - p.q0) * p.band_cap;
+    const double rq = (double)call.q_resid[q];
+    const double a = (double)p.bound_scan + (double)p.bound_rq * rq;
+    const double b = ((double)p.bound_rx + rq) * 1.001;
+
+    // A. k-th best lower bound: each lane keeps its k best (as order-mapped
+    //    keys with the entry's index, so equal values stay distinct), then k
+    //    rounds of the warp's largest key below the previous one
+    RegList<FS_MAX_K> lo;
+    lo.reset();
+    for (int e = lane; e < n; e += 32) {
+        const uint64_t key = band[e];
+        const double l = (double)key_score(key) - a - b * (double)db.resid[p.row0 + key_index(key)];
+        lo.offer((float)l == (float)l ? __double2float_rd(l) : -INFINITY, e, n, 0, -1);
+    }
+    double L = -INFINITY;
+    if (n >= k) {
+        uint64_t prev = ~0ull, kth = 0;
+        for (int r = 0; r < k; ++r) {
+            uint64_t best = 0;
+#pragma unroll
+            for (int e = 0; e < FS_MAX_K; ++e) {
+                const uint64_t v = lo.key(e);
+                if (v < prev && v > best) best = v;
+            }
+            best = warp_max_u64(best);
+            prev = best;
+            kth = best;
+        }
+        L = (double)key_score(kth);
+    }
+
+    // B. rescoring of every band row whose upper bound reaches L (kRescoreRows
+    //    at a time, warp-wide); its key's score becomes the FP32 cosine, the
+    //    other keys are cleared. Every lane keeps the same k best scores.
+    const float* qu = call.q_unit + (int64_t)q * db.fu;
+    RegList<FS_MAX_K> top;
+    top.reset();
+    int nres = 0;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        uint64_t key = e < n ? band[e] : 0;
+        bool in = false;
+        if (e < n) {
+            const double u = (double)key_score(key) + a + b * (double)db.resid[p.row0 + key_index(key)];
+            in = u >= L;
+            if (!in) band[e] = 0;
+        }
+        unsigned m = __ballot_sync(kFull, in);
+        nres += __popc(m);
+        while (m != 0) {
+            int64_t row[kRescoreRows];
+            int slot[kRescoreRows];
+#pragma unroll
+            for (int j = 0; j < kRescoreRows; ++j) {
+                slot[j] = m != 0 ? __ffs(m) - 1 : -1;
+                if (m != 0) m &= m - 1;
+                const uint64_t kj = __shfl_sync(kFull, key, slot[j] < 0 ? 0 : slot[j]);
+                row[j] = slot[j] < 0 ? -1 : p.row0 + key_index(kj);
+            }
+            float dot[kRescoreRows], dd[kRescoreRows];
+            rescore_rows<false>(db, qu, row, dot, dd, lane);
+#pragma unroll
+            for (int j = 0; j < kRescoreRows; ++j) {
+                if (slot[j] < 0) continue;
+                const uint32_t li = (uint32_t)(row[j] - p.row0);
+                top.offer(dot[j], li, ~0u, 0, -1);
+                if (lane == slot[j]) band[e] = make_key(dot[j], li);
+            }
+        }
+    }
+    __syncwarp();
+    if (nres == 0) return 0;
+
+    // C. the window: rescored rows within 2 E_r of the k-th best
+    const int kk = k < top.cnt ? k : top.cnt;
+    const float tk = top.kth_score(kk);
+    const float wlo = __double2float_ru((double)tk - 2.0 * (double)p.bound_rerank);
+    int nw = 0;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        const uint64_t key = e < n ? band[e] : 0;
+        const bool in = key != 0 && key_score(key) >= wlo;
+        const unsigned m = __ballot_sync(kFull, in);
+        const int pos = nw + __popc(m & ((1u << lane) - 1));
+        if (in && pos < kWindow) sh.widx[wid][pos] = key_index(key);
+        nw += __popc(m);
+    }
+    __syncwarp();
+    if (lane == 0) atomicAdd(&stats[kStatRerank], (unsigned long long)nres);
+    if (nw > kWindow) return -1;
+    return finish_window(db, call, sh, wid, lane, q, p, nw, stats);
+}
+
+// BAND: the FP8 scan's bands (two resident blocks per SM: the band pass
+// keeps two 16-entry lists per lane); else the candidate lists (at most 48
+// registers: five blocks per SM, fewer waves on large batches).
+template <bool BAND>
+__global__ void __launch_bounds__(kSelWarps * 32, BAND ? 2 : 5)
 k_select(DbView db, CallView call) {
     __shared__ SelShared sh;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -458,10 +608,15 @@ k_select(DbView db, CallView call) {
             }
             nout = c;
         } else {
-            const int nl = p.chunks * p.lists;
-            const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * nl * p.list_t;
-            const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
-            nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, nl, p.list_t, E, sh.stats);
+            if (BAND) {
+                nout = answer_from_band(db, call, sh, wid, lane, q, p, sh.stats);
+            } else {
+                const int nl = p.chunks * p.lists;
+                const uint64_t* cand = call.cand + p.cand0 + (int64_t)(q - p.q0) * nl * p.list_t;
+                const double E = (double)p.bound_scan + (double)p.bound_rq * (double)call.q_resid[q];
+                nout = answer_from_lists(db, call, sh, wid, lane, q, p, cand, nl, p.list_t, E,
+                                         sh.stats);
+            }
             if (nout < 0 && lane == 0) {
                 if (is_std_metric(db.metric)) {
                     // the binary64 scan answers it directly
@@ -791,7 +946,11 @@ cudaError_t launch_query_plan(const CallView& call, int32_t* q_plan, cudaStream_
 
 cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st) {
     if (call.nq == 0) return cudaSuccess;
-    k_select<<<(unsigned)ceil_div(call.nq, kSelWarps), kSelWarps * 32, 0, st>>>(db, call);
+    const unsigned grid = (unsigned)ceil_div(call.nq, kSelWarps);
+    if (db.prec == FS_FP8_E4M3 && db.metric == FS_COSINE)
+        k_select<true><<<grid, kSelWarps * 32, 0, st>>>(db, call);
+    else
+        k_select<false><<<grid, kSelWarps * 32, 0, st>>>(db, call);
     return cudaGetLastError();
 }
 

@@ -189,6 +189,19 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
     return r;
 }
 
+// TMA tile load by either CTA of a pair (cta_group::2) into its own shared
+// memory at dst, whose completion (bytes) is signalled on the mbarrier at
+// bar, a shared::cluster address that may be the peer CTA's (from mapa): both
+// CTAs of a pair fill one barrier of the CTA that issues the MMAs.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar, int32_t c0, int32_t c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
 // arrival on an mbarrier of another CTA of the cluster (address from mapa),
 // with the instruction's default semantics (release, CTA scope): the
 // cluster-scope release measured several times slower on this path
