@@ -279,7 +279,8 @@ def run_serving(args, fs, torch, dev, world, rank, local):
         tile_ms = e0.elapsed_time(e1)
         max_wait = tile_ms / 1e3 if args.max_wait_ms is None else args.max_wait_ms / 1e3
         srv = serve.Server(eng, arena_bytes=arena, slots=slots, max_batch=max_batch,
-                           min_batch=args.min_batch, max_wait_s=max_wait)
+                           min_batch=args.min_batch, max_wait_s=max_wait,
+                           max_queued=args.max_queued if args.max_queued > 0 else None)
         # warm-up: a few batches of every size class
         serve.run_open_loop(srv, serve.poisson_requests(pool, rate, min(0.05, duration), 1, 1024, 99))
         srv.stats = serve.ServerStats()
@@ -296,8 +297,16 @@ def run_serving(args, fs, torch, dev, world, rank, local):
         sampler.__enter__()
         wall = serve.run_open_loop(srv, reqs)
         sampler.__exit__(None, None, None)
-        nq = sum(r.queries.shape[0] for r in reqs)
-        res = {"wall_s": wall, "queries": nq, "requests": len(reqs), "batches": srv.stats.batches,
+        nq_offered = sum(r.queries.shape[0] for r in reqs)
+        nq = nq_offered - srv.stats.shed_queries
+        gpu_ms_1024 = sum(prof["ms"][s_] / max(1, prof["calls"][s_]) for s_ in prof["ms"])
+        res = {"wall_s": wall, "queries": nq, "offered_queries": nq_offered,
+               "requests": len(reqs), "batches": srv.stats.batches,
+               "shed_requests": srv.stats.shed_requests, "shed_queries": srv.stats.shed_queries,
+               "max_queued": args.max_queued,
+               "host_launch_ms_per_batch": srv.stats.launch_s * 1e3 / max(1, srv.stats.batches),
+               "host_retire_ms_per_batch": srv.stats.retire_s * 1e3 / max(1, srv.stats.batches),
+               "gpu_ms_per_1024_batch": gpu_ms_1024,
                "mean_batch": float(np.mean(srv.stats.batch_sizes)),
                "max_inflight": srv.stats.max_inflight,
                "admissions_blocked_by_memory": srv.stats.admissions_blocked_by_memory,
@@ -310,12 +319,24 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                "gpu_launches": int(round(prof["launches"] / max(1, prof["calls"]["prepare"])
                                          * srv.stats.batches))}
         res.update(serve.latency_summary(reqs))
-        # sample of answers for the oracle check
-        res["_sample"] = reqs[::max(1, len(reqs) // 16)][:16]
+        # sample of answers for the oracle check (answered requests)
+        done = [r for r in reqs if r.done is not None]
+        res["_sample"] = done[::max(1, len(done) // 16)][:16]
         db.close()
         del eng, srv
         return res
 
+    sweep = None
+    if args.sweep:
+        # offered rates from light load to far past capacity: served rate,
+        # latency and shed load at each (the headline line is --rate's)
+        sweep = []
+        for rate in [float(v) for v in args.sweep.split(",")]:
+            rr = serve_at(args.precision, rate, args.duration)
+            sweep.append({k_: v for k_, v in rr.items()
+                          if not k_.startswith("_") and k_ != "clocks"} | {"clocks": rr["clocks"]})
+            log(f"[serving] offered {rate:,.0f} q/s: served {rr['served_qps']:,.0f} q/s, "
+                f"p50 {rr['p50_ms']} ms, p99 {rr['p99_ms']} ms, shed {rr['shed_queries']:,} queries")
     r16 = serve_at(args.precision, args.rate, args.duration)
     r32 = None
     if not args.no_fp32_compare:
@@ -351,6 +372,7 @@ def run_serving(args, fs, torch, dev, world, rank, local):
                 "note": "the serving loop is end to end: host queries in, host results out"},
         "gpu_launches": r16["gpu_launches"], "roofline": roof,
         "serving": {kk: v for kk, v in r16.items() if not kk.startswith("_")},
+        "sweep": sweep,
         "vs_fp32_scan": None if r32 is None else {
             "fp32_offered_qps": args.fp32_rate, "fp32_served_qps": r32["served_qps"],
             "fp32_p50_ms": r32["p50_ms"], "fp32_p99_ms": r32["p99_ms"],
@@ -679,6 +701,10 @@ def main():
                     help="serving: offered rate for the plain FP32 path")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=4, help="serving: batches in flight")
+    ap.add_argument("--max-queued", type=int, default=8192,
+                    help="serving: queries the queue may hold; requests beyond are shed (0: no bound)")
+    ap.add_argument("--sweep", default=None,
+                    help="serving: comma-separated offered rates (q/s) to sweep before the headline run")
     ap.add_argument("--min-batch", type=int, default=128,
                     help="serving: queries a batch waits for while another is in flight")
     ap.add_argument("--max-wait-ms", type=float, default=None,

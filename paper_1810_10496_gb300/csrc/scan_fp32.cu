@@ -22,16 +22,25 @@ namespace {
 
 constexpr int BQ = kQTile;          // queries per item
 constexpr int BN = kFp32TileRows;   // rows per tile
-constexpr int BK = 8;               // features per pipeline step
+constexpr int BK = 16;              // features per pipeline step
 constexpr int THREADS = 256;
 constexpr int T = kListT;
-constexpr int SP = BN + 1;          // score-tile row pitch (odd: conflict free)
+// Row pitch of the operand and score tiles: 4 floats of padding make the
+// transposing operand stores, the float4 score stores and the filter's
+// float4 score reads free of bank conflicts (and keep rows 16-byte aligned).
+constexpr int P = 132;
 
+struct Operands {
+    float as[2][BK][P];   // queries, feature-major (double-buffered)
+    float bs[2][BK][P];   // database rows, feature-major
+};
 struct Smem {
-    float as[2][BK][BQ];
-    float bs[2][BK][BN];
-    float s[BQ][SP];
+    union {
+        Operands op;              // during the products
+        float s[BQ][P];           // the tile's scores, while the filter reads them
+    };
     uint64_t lists[T][THREADS];
+    float thr[THREADS];           // each list's current threshold (for the skip vote)
 };
 
 __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
@@ -46,8 +55,14 @@ __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t
 // METRIC: FS_COSINE and FS_EUCLIDEAN accumulate dot products (Euclidean then
 // subtracts the row term 1/2 |z_x|^2), FS_MANHATTAN accumulates |a - b| and
 // scores its negation; larger is nearer in every case.
+//
+// Per tile: the 128 x 128 products in registers (each thread 8 queries x 8
+// rows, features in order, FMA), then a block-wide vote: only when some score
+// reaches its list's threshold is the score tile written to shared memory
+// (over the idle operand buffers) for the list owners (thread = query x half
+// of the tile's rows) to filter.
 template <int METRIC>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2)
 k_scan_fp32(DbView db, CallView call) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -88,20 +103,26 @@ k_scan_fp32(DbView db, CallView call) {
         // (a zero cosine query, q_ss = 0, ties with every row and is answered
         // by the selection from row indices alone: it offers nothing)
         const bool qv = lq < nq_tile && call.q_ss[qbase + lq] != 0.0f;
+        // the vote's threshold of this list (read by other threads after the
+        // next barrier): a list of an absent or zero query never takes a row
+        sm.thr[tid] = qv ? -INFINITY : INFINITY;
         uint32_t* shared_p = call.shared_thr + qbase + (qv ? lq : 0);
         const float e2 =
             qv ? 2.0f * (p.bound_scan + p.bound_rq * call.q_resid[qbase + lq]) * 1.0001f : 0.0f;
         float published = -INFINITY;
 
-        // global-load mapping: one float4 of A and one of B per thread and step
-        const int ld_row = tid >> 1, ld_col = (tid & 1) * 4;
-        const float* qrow = call.q_unit + (int64_t)(qbase + ld_row) * fu + ld_col;
-        const bool q_ok = ld_row < nq_tile;
+        // global-load mapping: per step, two float4 of queries and two of rows
+        // (rows ld_row and ld_row + 64, features ld_col .. ld_col + 3)
+        const int ld_row = tid >> 2, ld_col = (tid & 3) * 4;
+        const float* qrow0 = call.q_unit + (int64_t)(qbase + ld_row) * fu + ld_col;
+        const float* qrow1 = qrow0 + (int64_t)64 * fu;
+        const bool q_ok0 = ld_row < nq_tile, q_ok1 = ld_row + 64 < nq_tile;
 
         for (int64_t tr = row_begin; tr < row_end; tr += BN) {
-            const int64_t brow = tr + ld_row;
-            const bool b_ok = brow < row_end;
-            const float* xrow = db.unit + brow * fu + ld_col;
+            const bool b_ok0 = tr + ld_row < row_end, b_ok1 = tr + ld_row + 64 < row_end;
+            const float* xrow0 = db.unit + (tr + ld_row) * fu + ld_col;
+            const float* xrow1 = xrow0 + (int64_t)64 * fu;
+            const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 
             float acc[8][8];
 #pragma unroll
@@ -109,31 +130,46 @@ k_scan_fp32(DbView db, CallView call) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-            float4 ra = q_ok ? *reinterpret_cast<const float4*>(qrow) : make_float4(0, 0, 0, 0);
-            float4 rb = b_ok ? __ldg(reinterpret_cast<const float4*>(xrow)) : make_float4(0, 0, 0, 0);
+            float4 ra0 = q_ok0 ? *reinterpret_cast<const float4*>(qrow0) : z4;
+            float4 ra1 = q_ok1 ? *reinterpret_cast<const float4*>(qrow1) : z4;
+            float4 rb0 = b_ok0 ? __ldg(reinterpret_cast<const float4*>(xrow0)) : z4;
+            float4 rb1 = b_ok1 ? __ldg(reinterpret_cast<const float4*>(xrow1)) : z4;
             int buf = 0;
             for (int k0 = 0; k0 < fu; k0 += BK) {
-                sm.as[buf][ld_col + 0][ld_row] = ra.x;
-                sm.as[buf][ld_col + 1][ld_row] = ra.y;
-                sm.as[buf][ld_col + 2][ld_row] = ra.z;
-                sm.as[buf][ld_col + 3][ld_row] = ra.w;
-                sm.bs[buf][ld_col + 0][ld_row] = rb.x;
-                sm.bs[buf][ld_col + 1][ld_row] = rb.y;
-                sm.bs[buf][ld_col + 2][ld_row] = rb.z;
-                sm.bs[buf][ld_col + 3][ld_row] = rb.w;
+                // fu is a multiple of 32, so every step is whole; features ld_col..+3
+                // of rows ld_row and ld_row + 64, stored feature-major
+                float (*as)[P] = sm.op.as[buf];
+                float (*bs)[P] = sm.op.bs[buf];
+                as[ld_col + 0][ld_row] = ra0.x;
+                as[ld_col + 1][ld_row] = ra0.y;
+                as[ld_col + 2][ld_row] = ra0.z;
+                as[ld_col + 3][ld_row] = ra0.w;
+                as[ld_col + 0][ld_row + 64] = ra1.x;
+                as[ld_col + 1][ld_row + 64] = ra1.y;
+                as[ld_col + 2][ld_row + 64] = ra1.z;
+                as[ld_col + 3][ld_row + 64] = ra1.w;
+                bs[ld_col + 0][ld_row] = rb0.x;
+                bs[ld_col + 1][ld_row] = rb0.y;
+                bs[ld_col + 2][ld_row] = rb0.z;
+                bs[ld_col + 3][ld_row] = rb0.w;
+                bs[ld_col + 0][ld_row + 64] = rb1.x;
+                bs[ld_col + 1][ld_row + 64] = rb1.y;
+                bs[ld_col + 2][ld_row + 64] = rb1.z;
+                bs[ld_col + 3][ld_row + 64] = rb1.w;
                 __syncthreads();
                 if (k0 + BK < fu) {
-                    ra = q_ok ? *reinterpret_cast<const float4*>(qrow + k0 + BK) : make_float4(0, 0, 0, 0);
-                    rb = b_ok ? __ldg(reinterpret_cast<const float4*>(xrow + k0 + BK))
-                              : make_float4(0, 0, 0, 0);
+                    ra0 = q_ok0 ? *reinterpret_cast<const float4*>(qrow0 + k0 + BK) : z4;
+                    ra1 = q_ok1 ? *reinterpret_cast<const float4*>(qrow1 + k0 + BK) : z4;
+                    rb0 = b_ok0 ? __ldg(reinterpret_cast<const float4*>(xrow0 + k0 + BK)) : z4;
+                    rb1 = b_ok1 ? __ldg(reinterpret_cast<const float4*>(xrow1 + k0 + BK)) : z4;
                 }
 #pragma unroll
                 for (int kk = 0; kk < BK; ++kk) {
                     float a[8], b[8];
-                    float4 t0 = *reinterpret_cast<const float4*>(&sm.as[buf][kk][ty * 4]);
-                    float4 t1 = *reinterpret_cast<const float4*>(&sm.as[buf][kk][64 + ty * 4]);
-                    float4 u0 = *reinterpret_cast<const float4*>(&sm.bs[buf][kk][tx * 4]);
-                    float4 u1 = *reinterpret_cast<const float4*>(&sm.bs[buf][kk][64 + tx * 4]);
+                    const float4 t0 = *reinterpret_cast<const float4*>(&as[kk][ty * 4]);
+                    const float4 t1 = *reinterpret_cast<const float4*>(&as[kk][64 + ty * 4]);
+                    const float4 u0 = *reinterpret_cast<const float4*>(&bs[kk][tx * 4]);
+                    const float4 u1 = *reinterpret_cast<const float4*>(&bs[kk][64 + tx * 4]);
                     a[0] = t0.x; a[1] = t0.y; a[2] = t0.z; a[3] = t0.w;
                     a[4] = t1.x; a[5] = t1.y; a[6] = t1.z; a[7] = t1.w;
                     b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
@@ -150,34 +186,49 @@ k_scan_fp32(DbView db, CallView call) {
                 }
                 buf ^= 1;
             }
-            __syncthreads();  // every thread is done with the previous score tile
-            // standardised metrics: the rows' terms and magnitudes (a row above
-            // a query's magnitude cap is provably not among its k nearest and
-            // scores -inf, since its FP32 score is outside the query's bound)
-            float rt[8], mg[8], cap[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-                const bool in = METRIC != FS_COSINE && tr + rj < row_end;
-                rt[j] = (METRIC == FS_EUCLIDEAN && in) ? db.row_term[tr + rj] : 0.0f;
-                mg[j] = in ? db.row_mag[tr + rj] : 0.0f;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
-                cap[i] = (METRIC != FS_COSINE && qi < nq_tile) ? call.q_scale[qbase + qi] : INFINITY;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+            // the scores of this thread's 8 queries x 8 rows (standardised
+            // metrics: minus the row term; a row above a query's magnitude cap
+            // is provably not among its k nearest and scores -inf, since its
+            // FP32 score is outside the query's bound)
+            if (METRIC != FS_COSINE) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int rj = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-                    float sc = METRIC == FS_MANHATTAN ? -acc[i][j]
-                               : (METRIC == FS_EUCLIDEAN ? acc[i][j] - rt[j] : acc[i][j]);
-                    if (METRIC != FS_COSINE && mg[j] > cap[i]) sc = -INFINITY;
-                    sm.s[qi][rj] = sc;
+                    const bool in = tr + rj < row_end;
+                    const float rt = (METRIC == FS_EUCLIDEAN && in) ? db.row_term[tr + rj] : 0.0f;
+                    const float mg = in ? db.row_mag[tr + rj] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+                        const float cap = qi < nq_tile ? call.q_scale[qbase + qi] : INFINITY;
+                        float sc = METRIC == FS_MANHATTAN ? -acc[i][j] : acc[i][j] - rt;
+                        if (mg > cap) sc = -INFINITY;
+                        acc[i][j] = sc;
+                    }
                 }
+            }
+            // does any score reach its list's threshold? (each list's owner wrote
+            // it after the previous tile; the shared bound only raises it)
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+                const float t0 = sm.thr[qi], t1 = sm.thr[qi + BQ];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) any |= acc[i][j] >= t0;
+#pragma unroll
+                for (int j = 4; j < 8; ++j) any |= acc[i][j] >= t1;
+            }
+            // every thread is done with the operand buffers (the score tile
+            // overlays them) and the vote is in
+            if (!__syncthreads_or(any)) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int qi = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+                *reinterpret_cast<float4*>(&sm.s[qi][tx * 4]) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                *reinterpret_cast<float4*>(&sm.s[qi][64 + tx * 4]) =
+                    make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
             }
             __syncthreads();
 
@@ -187,33 +238,38 @@ k_scan_fp32(DbView db, CallView call) {
             // (the initial bound, 0, maps to NaN: fmaxf then keeps thr_s)
             const float shared_s = qv ? unord_f32(__ldcg(shared_p)) : INFINITY;
             bool changed = false;
-            for (int j = 0; j < 64; ++j) {
-                const float sc = srow[j];
-                if (sc >= fmaxf(thr_s, shared_s)) {
-                    const int64_t row = col_row0 + j;
-                    const int32_t li = (int32_t)(row - p.row0);
-                    if (row < row_end && li != excl) {
-                        const uint64_t key = make_key(sc, (uint32_t)li);
-                        bool recompute = false;
-                        if (cnt < T) {
-                            sm.lists[cnt][tid] = key;
-                            ++cnt;
-                            recompute = (cnt == T);
-                        } else if (key > thr_key) {
-                            sm.lists[min_slot][tid] = key;
-                            recompute = true;
-                        }
-                        if (recompute) {
-                            uint64_t mn = ~0ull;
+            for (int j4 = 0; j4 < 64; j4 += 4) {
+                const float4 s4 = *reinterpret_cast<const float4*>(srow + j4);
+                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                            for (int e = 0; e < T; ++e) {
-                                uint64_t v = sm.lists[e][tid];
-                                if (v < mn) { mn = v; min_slot = e; }
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float sc = sv[jj];
+                    if (sc >= fmaxf(thr_s, shared_s)) {
+                        const int64_t row = col_row0 + j4 + jj;
+                        const int32_t li = (int32_t)(row - p.row0);
+                        if (row < row_end && li != excl) {
+                            const uint64_t key = make_key(sc, (uint32_t)li);
+                            bool recompute = false;
+                            if (cnt < T) {
+                                sm.lists[cnt][tid] = key;
+                                ++cnt;
+                                recompute = (cnt == T);
+                            } else if (key > thr_key) {
+                                sm.lists[min_slot][tid] = key;
+                                recompute = true;
                             }
-                            thr_key = mn;
-                            thr_s = key_score(mn);
+                            if (recompute) {
+                                uint64_t mn = ~0ull;
+#pragma unroll
+                                for (int e = 0; e < T; ++e) {
+                                    uint64_t v = sm.lists[e][tid];
+                                    if (v < mn) { mn = v; min_slot = e; }
+                                }
+                                thr_key = mn;
+                                thr_s = key_score(mn);
+                            }
+                            changed = true;
                         }
-                        changed = true;
                     }
                 }
             }
@@ -237,6 +293,12 @@ k_scan_fp32(DbView db, CallView call) {
                     published = bound;
                 }
             }
+            // this list's threshold for the next tile's vote (a list of a query
+            // outside the tile never takes a row)
+            // (both parts only rise, so the next filter's threshold is at least
+            // this: the vote never skips a tile the filter would take rows from)
+            sm.thr[tid] = fmaxf(thr_s, shared_s);
+            __syncthreads();   // the score tile is free for the next tile's operands
         }
 
         // publish this item's lists, sorted in descending order (empty entries,

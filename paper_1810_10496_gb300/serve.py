@@ -8,6 +8,11 @@ overlaps on the device (one CUDA stream per slot). Every transient byte of a
 batch (queries, workspace, outputs) is carved from one device arena; a batch
 is admitted only when it fits, which is the memory-based admission.
 
+Admission also sheds load: with `max_queued` set, a request that arrives
+while the queue already holds that many queries is refused at once (marked
+`shed`, never answered), so an overloaded server keeps bounded latency for
+the requests it accepts instead of a queue that grows without end.
+
 Each request's answer does not depend on which other requests share its
 batch: the selection is exact (a pure function of the score and index of
 each row), so a request alone and in the mix gets the same rows, distances
@@ -74,6 +79,7 @@ class Request:
     arrival: float                     # seconds (server clock)
     queries: np.ndarray                # [b, F] float32
     done: float | None = None
+    shed: bool = False                 # refused at admission (queue full)
     idx: np.ndarray | None = None
     dist: np.ndarray | None = None
     seqs: np.ndarray | None = None
@@ -101,6 +107,10 @@ class ServerStats:
     max_arena_used: int = 0
     admissions_blocked_by_memory: int = 0
     held_for_fill: int = 0
+    shed_requests: int = 0             # refused at arrival: the queue was full
+    shed_queries: int = 0
+    launch_s: float = 0.0              # host seconds spent launching batches
+    retire_s: float = 0.0              # host seconds spent handing results back
     batch_sizes: list = field(default_factory=list)
 
 
@@ -116,8 +126,9 @@ class Server:
     full tile. With nothing in flight a batch starts at once."""
 
     def __init__(self, engine, arena_bytes: int, slots: int = 4, max_batch: int = 1024,
-                 min_batch: int = 1, max_wait_s: float = 0.0):
+                 min_batch: int = 1, max_wait_s: float = 0.0, max_queued: int | None = None):
         self.engine = engine
+        self.max_queued = max_queued
         self.arena = Arena(arena_bytes)
         self.slots = slots
         self.max_batch = max_batch
@@ -129,18 +140,27 @@ class Server:
         self.free_slots = list(range(slots))
         self.stats = ServerStats()
 
-    def submit(self, req: Request):
-        if req.queries.shape[0] > self.max_batch:
+    def submit(self, req: Request) -> bool:
+        """Queues `req`; False (and `req.shed` set) when the queue is full."""
+        n = req.queries.shape[0]
+        if n > self.max_batch:
             raise ValueError("a request may not exceed max_batch queries")
-        if self.engine.batch_bytes(req.queries.shape[0]) > self.arena.size:
+        if self.engine.batch_bytes(n) > self.arena.size:
             raise ValueError("a request needs more device memory than the whole arena")
+        if self.max_queued is not None and self.queued + n > self.max_queued:
+            req.shed = True
+            self.stats.shed_requests += 1
+            self.stats.shed_queries += n
+            return False
         self.queue.append(req)
-        self.queued += req.queries.shape[0]
+        self.queued += n
+        return True
 
     def _complete(self, now_fn):
         still = []
         for b in self.inflight:
             if self.engine.done(b.handle):
+                t0 = time.perf_counter()
                 res = self.engine.results(b.handle)
                 t = now_fn()
                 row = 0
@@ -151,6 +171,7 @@ class Server:
                     row += n
                 self.arena.release(*b.mem)
                 self.free_slots.append(b.slot)
+                self.stats.retire_s += time.perf_counter() - t0
             else:
                 still.append(b)
         self.inflight = still
@@ -179,8 +200,10 @@ class Server:
                 self.queue.popleft()
             self.queued -= nq
             slot = self.free_slots.pop()
+            t0 = time.perf_counter()
             q = np.concatenate([r.queries for r in take]) if len(take) > 1 else take[0].queries
             handle = self.engine.launch(q, mem[0], slot)
+            self.stats.launch_s += time.perf_counter() - t0
             self.inflight.append(_Batch(take, nq, mem, handle, slot))
             st = self.stats
             st.batches += 1
@@ -236,7 +259,10 @@ def run_open_loop(server: Server, requests, clock=time.perf_counter, max_wall_s:
 
 
 def latency_summary(requests):
+    """Latency percentiles of the answered requests (shed ones have none)."""
     lat = np.array([r.latency for r in requests if r.latency is not None]) * 1e3
+    if lat.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "mean_ms": None, "max_ms": None, "n": 0}
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "n": int(len(lat))}
 

@@ -151,3 +151,40 @@ def test_min_fill_holds_small_batches_only_while_busy():
     assert max(r.latency for r in reqs) < 0.003 + 3 * 0.005 + 0.01
     for r in reqs:
         assert np.array_equal(r.idx, (r.queries[:, :3] * 10).astype(np.int32))
+
+
+def test_overload_sheds_at_admission_and_bounds_latency():
+    """Offered load far above capacity: with a queue bound, requests beyond
+    it are refused at arrival (never answered), every accepted request is
+    answered and routed, and the accepted requests' latency stays bounded by
+    the queue's work; without a bound nothing is refused and the latency
+    grows with the backlog."""
+    def run(max_queued):
+        clock = FakeClock()
+        eng = FakeEngine(clock, latency=0.01)
+        srv = serve.Server(eng, arena_bytes=400_000, slots=2, max_batch=64,
+                           max_queued=max_queued)
+        rng = np.random.default_rng(9)
+        reqs = [serve.Request(i, 0.0002 * i, rng.integers(0, 9, size=(8, 8)).astype(np.float32))
+                for i in range(600)]
+        serve.run_open_loop(srv, reqs, clock=clock, max_wall_s=1e6)
+        return srv, reqs
+
+    srv, reqs = run(128)
+    shed = [r for r in reqs if r.shed]
+    kept = [r for r in reqs if not r.shed]
+    assert srv.stats.shed_requests == len(shed) > 0
+    assert srv.stats.shed_queries == sum(r.queries.shape[0] for r in shed)
+    assert all(r.done is None and r.idx is None for r in shed)
+    assert all(r.done is not None for r in kept)
+    for r in kept:
+        assert np.array_equal(r.idx, (r.queries[:, :3] * 10).astype(np.int32))
+    assert srv.stats.queries == sum(r.queries.shape[0] for r in kept)
+    bounded = max(r.latency for r in kept)
+    summary = serve.latency_summary(reqs)
+    assert summary["n"] == len(kept)
+
+    srv2, reqs2 = run(None)
+    assert srv2.stats.shed_requests == 0 and all(r.done is not None for r in reqs2)
+    assert max(r.latency for r in reqs2) > 2 * bounded
+    assert srv.stats.launch_s >= 0.0 and srv.stats.retire_s >= 0.0
