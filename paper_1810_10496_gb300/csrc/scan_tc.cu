@@ -484,168 +484,197 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 bool offered = false;   // the list may have changed in this tile
                 // FP8 threshold on h = s + fb r_x (the upper bound minus fa)
                 const float shared_h = shared_s - fa;
-#pragma unroll 1
-                for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 64) {
-                    uint32_t r0[32], r1[32];
-                    tmem_ld_32x32b_x32(taddr + c0, r0);
-                    tmem_ld_32x32b_x32(taddr + c0 + 32, r1);
-                    tmem_ld_wait();
-                    // FP8: v = acc * s_row (the codes are unit elements divided by
-                    // their row's scale, so the row scale belongs to each score before
-                    // any maximum); BF16: v = acc
-                    float v[64];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        v[j] = __uint_as_float(r0[j]);
-                        v[32 + j] = __uint_as_float(r1[j]);
+                // The thread's 128 columns in four chunks of 32, software-pipelined
+                // through two register buffers: the next chunk's TMEM load is in
+                // flight while this chunk is filtered, and the accumulator is freed
+                // as soon as the last chunk has landed, before it is filtered.
+                constexpr int kCW = 32, kCG = kCW / 8;
+                static_assert(kHalfCols == 4 * kCW, "four chunks per half tile");
+                auto release = [&]() {
+                    // every TMEM load of this tile has landed (tcgen05.wait::ld)
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const uint32_t bar = r_tmem_empty0 + acc * (uint32_t)sizeof(uint64_t);
+                        if (PAIR && !leader)
+                            mbar_arrive_cluster(bar);
+                        else
+                            mbar_arrive(bar);
                     }
-                    if (FP8) {
-                        const float4* s4 = reinterpret_cast<const float4*>(&wsx[ew][c0 - half * kHalfCols]);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float4 sc4 = s4[j];
-                            v[4 * j] *= sc4.x;
-                            v[4 * j + 1] *= sc4.y;
-                            v[4 * j + 2] *= sc4.z;
-                            v[4 * j + 3] *= sc4.w;
-                        }
-                    }
-                    float gm[8];
-#pragma unroll
-                    for (int g = 0; g < 8; ++g) {
-                        const float a = fmax3(v[8 * g], v[8 * g + 1], v[8 * g + 2]);
-                        const float b = fmax3(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]);
-                        const float mx = fmax3(a, b, fmaxf(v[8 * g + 6], v[8 * g + 7]));
+                };
+                auto filter = [&](const uint32_t (&rbuf)[kCW], const int c0) {
+                        // FP8: v = acc * s_row (the codes are unit elements divided by
+                        // their row's scale, so the row scale belongs to each score before
+                        // any maximum); BF16: v = acc
+                        float v[kCW];
+    #pragma unroll
+                        for (int j = 0; j < kCW; ++j) v[j] = __uint_as_float(rbuf[j]);
                         if (FP8) {
-                            // an upper bound on h over the group: its largest scaled
-                            // score times the query scale (a non-negative factor), plus
-                            // fb times the group's largest residual; each step rounds
-                            // monotonically, so no h of the group exceeds it
-                            const int gi = ((c0 - half * kHalfCols) >> 3) + g;
-                            gm[g] = fmaf(fb, wgrx[ew][gi], mx * sq);
-                        } else {
-                            gm[g] = mx;
-                        }
-                    }
-                    const float m = fmax3(fmax3(gm[0], gm[1], gm[2]), fmax3(gm[3], gm[4], gm[5]),
-                                          fmaxf(gm[6], gm[7]));
-                    if (FP8) {
-                        float thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa : -INFINITY,
-                                          shared_h);
-                        if (__any_sync(0xffffffffu, m >= thr)) {
-                            // Group by group (a loop kept rolled: the group's 8 scores
-                            // are rotated to the front of v, so the body is compiled
-                            // once and stays in the instruction cache):
-                            // 1: the rows' lower bounds g = s - fb r_x join the list of
-                            //    the LT best (a row's g is at most its h, so a group
-                            //    whose bound on h is under thr holds no g the list
-                            //    keeps), and the threshold tightens;
-                            // 2: the rows whose h = s + fb r_x reaches it are appended
-                            //    to the band (the list's own k best are among them:
-                            //    their h is at least their g).
-#pragma unroll 1
-                            for (int g = 0; g < 8; ++g) {
-                                if (__any_sync(0xffffffffu, gm[0] >= thr)) {
-                                    const int lcg = c0 + 8 * g - half * kHalfCols;   // in the half
-                                    const int64_t row0g = tile_row0 + c0 + 8 * g;
-                                    if (gm[0] >= thr) {
-#pragma unroll
-                                        for (int i = 0; i < 8; ++i) {
-                                            const int64_t row = row0g + i;
-                                            if (row < w.row_end && (int)(row - w.p.row0) != excl)
-                                                st.offer(fmaf(-fb, wrx[ew][lcg + i], v[i] * sq), 0, 1, 0, -1);
-                                        }
-                                    }
-                                    thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa
-                                                                : -INFINITY,
-                                                shared_h);
-                                    uint32_t bits = 0;
-#pragma unroll
-                                    for (int i = 0; i < 8; ++i) {
-                                        const float h = fmaf(fb, wrx[ew][lcg + i], v[i] * sq);
-                                        const int64_t row = row0g + i;
-                                        const bool in = h >= thr && row < w.row_end &&
-                                                        (int)(row - w.p.row0) != excl;
-                                        bits |= (in ? 1u : 0u) << i;
-                                    }
-                                    if (bits != 0) {
-                                        int at = atomicAdd(band_cnt, __popc(bits));
-                                        for (uint32_t b = bits; b != 0; b &= b - 1, ++at) {
-                                            const int i = __ffs(b) - 1;
-                                            // v[i] without a run-time register index
-                                            float vi = v[0];
-#pragma unroll
-                                            for (int i2 = 1; i2 < 8; ++i2)
-                                                if (i2 == i) vi = v[i2];
-                                            const float sc = vi * sq;
-                                            const uint32_t li = (uint32_t)(row0g + i - w.p.row0);
-                                            if (at < w.p.band_cap) band[at] = make_key(sc, li);
-                                            // the best lower bound of its class
-                                            const int cls = (int)(li % (uint32_t)w.p.k);
-                                            const float gl = fmaf(-fb, wrx[ew][lcg + i], sc);
-#pragma unroll
-                                            for (int c = 0; c < LT; ++c)
-                                                if (c == cls && gl > cbest[c]) {
-                                                    cbest[c] = gl;
-                                                    cdirty |= 1u << c;
-                                                }
-                                        }
-                                    }
-                                }
-                                // the next group to the front
-#pragma unroll
-                                for (int j = 0; j < 56; ++j) v[j] = v[j + 8];
-#pragma unroll
-                                for (int j = 0; j < 7; ++j) gm[j] = gm[j + 1];
+                            const float4* s4 = reinterpret_cast<const float4*>(&wsx[ew][c0 - half * kHalfCols]);
+    #pragma unroll
+                            for (int j = 0; j < kCW / 4; ++j) {
+                                const float4 sc4 = s4[j];
+                                v[4 * j] *= sc4.x;
+                                v[4 * j + 1] *= sc4.y;
+                                v[4 * j + 2] *= sc4.z;
+                                v[4 * j + 3] *= sc4.w;
                             }
                         }
-                    } else {
-                        float thr = fmaxf(st.thr_s, shared_s);
-                        if (__any_sync(0xffffffffu, m >= thr)) {
-                            // group by group, with the threshold as it stands (a list
-                            // that is filling tightens after every group): each lane
-                            // collects its passing columns of the group, then every
-                            // lane takes its next candidate in the same round
-#pragma unroll
-                            for (int g = 0; g < 8; ++g) {
-                                if (__any_sync(0xffffffffu, gm[g] >= thr)) {
-                                    uint32_t bits = 0;
-#pragma unroll
-                                    for (int i = 0; i < 8; ++i)
-                                        bits |= (v[8 * g + i] >= thr ? 1u : 0u) << i;
-                                    while (__any_sync(0xffffffffu, bits != 0)) {
+                        float gm[kCG];
+    #pragma unroll
+                        for (int g = 0; g < kCG; ++g) {
+                            const float a = fmax3(v[8 * g], v[8 * g + 1], v[8 * g + 2]);
+                            const float b = fmax3(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]);
+                            const float mx = fmax3(a, b, fmaxf(v[8 * g + 6], v[8 * g + 7]));
+                            if (FP8) {
+                                // an upper bound on h over the group: its largest scaled
+                                // score times the query scale (a non-negative factor), plus
+                                // fb times the group's largest residual; each step rounds
+                                // monotonically, so no h of the group exceeds it
+                                const int gi = ((c0 - half * kHalfCols) >> 3) + g;
+                                gm[g] = fmaf(fb, wgrx[ew][gi], mx * sq);
+                            } else {
+                                gm[g] = mx;
+                            }
+                        }
+                        static_assert(kCG == 4, "four groups of 8 per chunk");
+                        const float m = fmaxf(fmax3(gm[0], gm[1], gm[2]), gm[3]);
+                        if (FP8) {
+                            float thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa : -INFINITY,
+                                              shared_h);
+                            if (__any_sync(0xffffffffu, m >= thr)) {
+                                // Group by group (a loop kept rolled: the group's 8 scores
+                                // are rotated to the front of v, so the body is compiled
+                                // once and stays in the instruction cache):
+                                // 1: the rows' lower bounds g = s - fb r_x join the list of
+                                //    the LT best (a row's g is at most its h, so a group
+                                //    whose bound on h is under thr holds no g the list
+                                //    keeps), and the threshold tightens;
+                                // 2: the rows whose h = s + fb r_x reaches it are appended
+                                //    to the band (the list's own k best are among them:
+                                //    their h is at least their g).
+    #pragma unroll 1
+                                for (int g = 0; g < kCG; ++g) {
+                                    if (__any_sync(0xffffffffu, gm[0] >= thr)) {
+                                        const int lcg = c0 + 8 * g - half * kHalfCols;   // in the half
+                                        const int64_t row0g = tile_row0 + c0 + 8 * g;
+                                        if (gm[0] >= thr) {
+    #pragma unroll
+                                            for (int i = 0; i < 8; ++i) {
+                                                const int64_t row = row0g + i;
+                                                if (row < w.row_end && (int)(row - w.p.row0) != excl)
+                                                    st.offer(fmaf(-fb, wrx[ew][lcg + i], v[i] * sq), 0, 1, 0, -1);
+                                            }
+                                        }
+                                        thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa
+                                                                    : -INFINITY,
+                                                    shared_h);
+                                        uint32_t bits = 0;
+    #pragma unroll
+                                        for (int i = 0; i < 8; ++i) {
+                                            const float h = fmaf(fb, wrx[ew][lcg + i], v[i] * sq);
+                                            const int64_t row = row0g + i;
+                                            const bool in = h >= thr && row < w.row_end &&
+                                                            (int)(row - w.p.row0) != excl;
+                                            bits |= (in ? 1u : 0u) << i;
+                                        }
                                         if (bits != 0) {
-                                            const int i = __ffs(bits) - 1;
-                                            bits &= bits - 1;
-                                            const float a0 = (i & 1) ? v[8 * g + 1] : v[8 * g];
-                                            const float a1 = (i & 1) ? v[8 * g + 3] : v[8 * g + 2];
-                                            const float a2 = (i & 1) ? v[8 * g + 5] : v[8 * g + 4];
-                                            const float a3 = (i & 1) ? v[8 * g + 7] : v[8 * g + 6];
-                                            const float b0 = (i & 2) ? a1 : a0;
-                                            const float b1 = (i & 2) ? a3 : a2;
-                                            const float sc = (i & 4) ? b1 : b0;
-                                            if (sc >= thr) {
-                                                st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
-                                                         w.p.row0, excl);
-                                                thr = fmaxf(st.thr_s, shared_s);
-                                                offered = true;
+                                            int at = atomicAdd(band_cnt, __popc(bits));
+                                            for (uint32_t b = bits; b != 0; b &= b - 1, ++at) {
+                                                const int i = __ffs(b) - 1;
+                                                // v[i] without a run-time register index
+                                                float vi = v[0];
+    #pragma unroll
+                                                for (int i2 = 1; i2 < 8; ++i2)
+                                                    if (i2 == i) vi = v[i2];
+                                                const float sc = vi * sq;
+                                                const uint32_t li = (uint32_t)(row0g + i - w.p.row0);
+                                                if (at < w.p.band_cap) band[at] = make_key(sc, li);
+                                                // the best lower bound of its class
+                                                const int cls = (int)(li % (uint32_t)w.p.k);
+                                                const float gl = fmaf(-fb, wrx[ew][lcg + i], sc);
+    #pragma unroll
+                                                for (int c = 0; c < LT; ++c)
+                                                    if (c == cls && gl > cbest[c]) {
+                                                        cbest[c] = gl;
+                                                        cdirty |= 1u << c;
+                                                    }
+                                            }
+                                        }
+                                    }
+                                    // the next group to the front
+    #pragma unroll
+                                    for (int j = 0; j < kCW - 8; ++j) v[j] = v[j + 8];
+    #pragma unroll
+                                    for (int j = 0; j < kCG - 1; ++j) gm[j] = gm[j + 1];
+                                }
+                            }
+                        } else {
+                            float thr = fmaxf(st.thr_s, shared_s);
+                            if (__any_sync(0xffffffffu, m >= thr)) {
+                                // group by group, with the threshold as it stands (a list
+                                // that is filling tightens after every group): each lane
+                                // collects its passing columns of the group, then every
+                                // lane takes its next candidate in the same round
+    #pragma unroll
+                                for (int g = 0; g < kCG; ++g) {
+                                    if (__any_sync(0xffffffffu, gm[g] >= thr)) {
+                                        uint32_t bits = 0;
+    #pragma unroll
+                                        for (int i = 0; i < 8; ++i)
+                                            bits |= (v[8 * g + i] >= thr ? 1u : 0u) << i;
+                                        while (__any_sync(0xffffffffu, bits != 0)) {
+                                            if (bits != 0) {
+                                                const int i = __ffs(bits) - 1;
+                                                bits &= bits - 1;
+                                                const float a0 = (i & 1) ? v[8 * g + 1] : v[8 * g];
+                                                const float a1 = (i & 1) ? v[8 * g + 3] : v[8 * g + 2];
+                                                const float a2 = (i & 1) ? v[8 * g + 5] : v[8 * g + 4];
+                                                const float a3 = (i & 1) ? v[8 * g + 7] : v[8 * g + 6];
+                                                const float b0 = (i & 2) ? a1 : a0;
+                                                const float b1 = (i & 2) ? a3 : a2;
+                                                const float sc = (i & 4) ? b1 : b0;
+                                                if (sc >= thr) {
+                                                    st.offer(sc, tile_row0 + c0 + 8 * g + i, w.row_end,
+                                                             w.p.row0, excl);
+                                                    thr = fmaxf(st.thr_s, shared_s);
+                                                    offered = true;
+                                                }
                                             }
                                         }
                                     }
                                 }
                             }
                         }
-                    }
                     __syncwarp();
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    const uint32_t bar = r_tmem_empty0 + acc * (uint32_t)sizeof(uint64_t);
-                    if (PAIR && !leader)
-                        mbar_arrive_cluster(bar);
-                    else
-                        mbar_arrive(bar);
+                };
+                if (FP8) {
+                    // one buffer (the FP8 filter's own state needs the registers)
+#pragma unroll 1
+                    for (int cc = 0; cc < 4; ++cc) {
+                        uint32_t ra[kCW];
+                        tmem_ld_32x32b_x32(taddr + half * kHalfCols + cc * kCW, ra);
+                        tmem_ld_wait();
+                        if (cc == 3) release();
+                        filter(ra, half * kHalfCols + cc * kCW);
+                    }
+                } else {
+                    uint32_t ra[kCW], rb[kCW];
+                    tmem_ld_32x32b_x32(taddr + half * kHalfCols, ra);
+                    tmem_ld_wait();
+#pragma unroll 1
+                    for (int cc = 0; cc < 4; cc += 2) {
+                        const int c0 = half * kHalfCols + cc * kCW;
+                        tmem_ld_32x32b_x32(taddr + c0 + kCW, rb);
+                        filter(ra, c0);
+                        tmem_ld_wait();
+                        if (cc + 2 < 4)
+                            tmem_ld_32x32b_x32(taddr + c0 + 2 * kCW, ra);
+                        else
+                            release();
+                        filter(rb, c0 + kCW);
+                        if (cc + 2 < 4) tmem_ld_wait();
+                    }
                 }
                 if (FP8) {
                     // the class slots that improved: g - fa, rounded down (the bound

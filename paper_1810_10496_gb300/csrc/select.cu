@@ -833,8 +833,10 @@ __global__ void k_fallback_merge(DbView db, CallView call) {
     __syncthreads();
     const int nfb = *call.fb2_count;
     const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (slot < nfb) {
+    // a fixed grid strides over the queries (usually none: the grid then
+    // returns at once)
+    for (int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); slot < nfb;
+         slot += gridDim.x * (blockDim.x >> 5)) {
         const int q = call.fb2_list[slot];
         const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
@@ -965,7 +967,7 @@ cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
     k_fallback_scan<<<num_sms * 2, kFbThreads, 0, st>>>(db, call);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_fallback_merge<<<(unsigned)ceil_div(call.nq, 8), 256, 0, st>>>(db, call);
+    k_fallback_merge<<<num_sms, 256, 0, st>>>(db, call);
     return cudaGetLastError();
 }
 
