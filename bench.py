@@ -43,11 +43,34 @@ UNIT = "pairs/s"
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture of the current version of that kernel, keyed by (kernel, workload,
-# precision); absent (reported as null) until captured. Source: the matching
-# summary under profiles/.
+# precision), with the scan plan tuning it was captured under (None: the
+# default plan); absent (reported as null) until captured. Source: the
+# matching summary under profiles/.
 TRAFFIC_BYTES = {
-    ("scan_bf16", "fp32_scale", "bf16"): 314.50e6,   # profiles/scan_bf16_fp32_scale.md
+    # a 1,048,576-row cut (594.1 MB per launch) scaled by the rows to the full
+    # 16,777,216 rows: profiles/scan_bf16_precision.md
+    ("scan_bf16", "precision", "bf16"): (9.44e9, None),
+    # the first 64 of the 512 databases (651.5 MB per launch) scaled by the rows
+    # to all 19,138,960: profiles/scan_bf16_batching.md
+    ("scan_bf16", "batching", "bf16"): (5.36e9, {"items_per_block": 1, "list_len": 16}),
+    ("scan_fp8", "fp32_scale", "fp8"): (190.6e6, None),     # profiles/scan_fp8_fp32_scale.md
+    ("scan_fp32", "fp32_scale", "fp32"): (632.7e6, None),   # profiles/scan_fp32_fp32_scale.md
 }
+
+
+def captured_traffic(kernel, workload, prec, metric, tuning, full_size):
+    """The captured DRAM bytes per launch when this run matches the capture:
+    the whole workload, the cosine and the captured plan tuning."""
+    got = TRAFFIC_BYTES.get((kernel, workload, prec))
+    if got is None or not full_size or metric != "cosine":
+        return None
+    nbytes, plan = got
+    if plan is None:
+        return nbytes if tuning is None else None
+    if tuning is None:
+        return None
+    used = {k: v for k, v in tuning.items() if v}
+    return nbytes if all(used.get(k) == v for k, v in plan.items()) else None
 
 
 def log(*a):
@@ -215,32 +238,70 @@ def oracle_sample_size(w, seconds: float, lo: int, hi: int) -> int:
     return int(min(hi, w.q, max(lo, round(seconds / max(per_query, 1e-9)))))
 
 
+# The oracle passes once over the rows it is given per call, whatever the
+# number of queries (norms and binary64 copies per 65,536-row chunk): about
+# 7.6 ns per row element on the machine's host cores (32.5 s for 16,777,216 x 256).
+ORACLE_PASS_S_PER_ELEMENT = 7.6e-9
+
+
+def oracle_window_sample(w, nq, rows, step, metric="cosine"):
+    """Time the oracle on `nq` queries against a window of `rows` consecutive
+    rows of a one-database workload (the window moves with `step`); returns
+    the seconds and the (query, row) pairs."""
+    import oracle
+    rng = np.random.default_rng(step)
+    pick = np.sort(rng.choice(w.q, size=min(nq, w.q), replace=False))
+    lo = (step * rows) % max(1, w.n - rows + 1)
+    hi = lo + rows
+    off = w.seq_off[lo:hi + 1] - w.seq_off[lo]
+    ids = w.seq_ids[w.seq_off[lo]:w.seq_off[hi]]
+    t0 = time.perf_counter()
+    if metric == "cosine":
+        oracle.recommend(w.x[lo:hi], w.queries[pick], w.k[0], off, ids, 128)
+    else:
+        oracle.knn_metric(w.x[lo:hi], w.queries[pick], w.k[0], metric)
+    return time.perf_counter() - t0, len(pick) * rows
+
+
 def run_reference(args):
     world, rank, _ = setup_dist()
     if rank != 0:
         return 0
     w = fsgen.make(args.workload, workers=min(16, _NCPU), n=args.n, q=args.q, n_db=args.n_db)
-    # each step a bounded sample: about 4 s of oracle work
-    nq = args.ref_sample if args.ref_sample else oracle_sample_size(w, 4.0, 1, 32)
+    # each step a bounded sample of about 4 s of oracle work: some queries
+    # against their whole databases, or, where one pass over a database takes
+    # longer (the oracle's cost per call is a pass over its rows), against a
+    # window of its rows that moves from step to step
+    budget = 4.0
+    nq = args.ref_sample if args.ref_sample else oracle_sample_size(w, budget, 1, 32)
+    window = None
+    if w.n_seg == 1 and w.n * w.f * ORACLE_PASS_S_PER_ELEMENT > budget:
+        window = int(min(w.n, max(65536, budget / (w.f * ORACLE_PASS_S_PER_ELEMENT) // 65536 * 65536)))
+        nq = args.ref_sample if args.ref_sample else 8
     times, pairs = [], 0
     for s in range(args.warmup + args.steps):
-        _, _, dt, pr = oracle_sample(w, nq, seed=s, metric=args.metric)
+        if window:
+            dt, pr = oracle_window_sample(w, nq, window, s, metric=args.metric)
+        else:
+            _, _, dt, pr = oracle_sample(w, nq, seed=s, metric=args.metric)
         if s >= args.warmup:
             times.append(dt)
             pairs += pr
     nq = min(nq, w.q)
     sec = float(np.sum(times))
     value = pairs / sec
+    sample = (f"{nq} of {w.q:,} queries per step against a window of {window:,} of the "
+              f"{w.n:,} rows (moving each step)" if window else
+              f"{nq} of {w.q:,} queries per step, each against its whole database")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(w), "sample": f"{nq} queries per step"},
-        "queries_per_s": nq * args.steps / sec,
+        "config": {"workload": workload_desc(w), "sample": sample},
+        "queries_per_s": pairs / w.n / sec if window is None and w.n_seg == 1 else None,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": _NCPU, "kind": "oracle",
-                         "sample": f"{nq} of {w.q:,} queries per step, each against its whole "
-                                   f"database"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -580,8 +641,12 @@ def run_ours(args):
                 "peak_source": f"{peak_src} bf16 burst" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # the captured figure holds for the captured configuration only
-    same_config = args.n is None and args.q is None and args.n_db is None and not tuned
-    roof["traffic"] = TRAFFIC_BYTES.get((f"scan_{prec}", args.workload, prec)) if same_config else None
+    full_size = args.n is None and args.q is None and args.n_db is None
+    roof["traffic"] = captured_traffic(f"scan_{prec}", args.workload, prec, args.metric,
+                                       tuned[prec]["tuning"] if tuned else None, full_size)
+    if prec != "fp32" and w.n_seg == 1:
+        roof["frac_of_sustained"] = roof["achieved"] / (peaks["bf16_tflops_sustained"] *
+                                                        (2.0 if prec == "fp8" else 1.0))
     roof["kernel"] = f"scan ({prec})"
     roof["kernel_ms"] = scan_ms
     roof["stage_ms_per_step"] = {s: prof["ms"][s] / max(1, prof["calls"][s]) for s in prof["ms"]}

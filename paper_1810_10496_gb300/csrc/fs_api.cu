@@ -351,13 +351,15 @@ fs_status make_plan(const fs_db* db, int32_t nq, const int32_t* q_seg_off, const
         p.list_t = pl.list_t;
         if (db->prec == FS_FP8_E4M3) {
             // band capacity per query: the rows within the FP8 error of the k-th
-            // best (measured: a few hundred per million rows) plus the rows each
-            // list accepts before its running bound forms (many lists of one
-            // tile each, all in the first wave, are the worst case); never more
-            // rows than the segment has, so a segment of up to 8,192 rows
-            // cannot overflow
-            const int64_t want = std::min<int64_t>(65536, std::max<int64_t>(8192,
-                                                   round_up(ceil_div(p.nrows, 64), 256)));
+            // best (measured: a few hundred per million rows; the buffer allows
+            // one in 64) plus the rows each of the query's lists (two per row
+            // chunk) may accept before its running bound forms (measured up to
+            // about 50 in a list's first tile; many lists of one tile each, all
+            // in the first wave, are the worst case); never more rows than the
+            // segment has, so a segment of up to 8,192 rows cannot overflow
+            const int64_t want = std::min<int64_t>(
+                65536, std::max<int64_t>(8192, round_up(128 * (int64_t)p.chunks +
+                                                        ceil_div(p.nrows, 64), 256)));
             p.band_cap = (int32_t)std::min<int64_t>(want, std::max<int64_t>(round_up(p.nrows, 32), 32));
         }
         if (is_std_metric(db->metric)) {

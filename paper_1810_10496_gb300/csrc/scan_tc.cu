@@ -395,7 +395,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             const float sq = FP8 ? (qvalid ? call.q_scale[w.qbase + lq] : 0.0f) : 1.0f;
             const float rq = qvalid ? call.q_resid[w.qbase + lq] : 0.0f;
             // BF16: the list of the LT best (score, row) pairs. FP8: the LT best
-            // lower bounds g = s - b r_x of the rows seen (rows unused).
+            // per-group lower bounds g = s - b r_x of the rows seen (rows unused).
             RegList<LT> st;
             st.reset();
 
@@ -540,35 +540,41 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         static_assert(kCG == 4, "four groups of 8 per chunk");
                         const float m = fmaxf(fmax3(gm[0], gm[1], gm[2]), gm[3]);
                         if (FP8) {
+                            // the threshold on h: the larger of two lower bounds on the
+                            // k-th best lower bound, each reached by k distinct band rows:
+                            // the k-th best of this list (below) and the shared class slots
                             float thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa : -INFINITY,
                                               shared_h);
                             if (__any_sync(0xffffffffu, m >= thr)) {
                                 // Group by group (a loop kept rolled: the group's 8 scores
                                 // are rotated to the front of v, so the body is compiled
                                 // once and stays in the instruction cache):
-                                // 1: the rows' lower bounds g = s - fb r_x join the list of
-                                //    the LT best (a row's g is at most its h, so a group
-                                //    whose bound on h is under thr holds no g the list
-                                //    keeps), and the threshold tightens;
+                                // 1: the group's best lower bound g = s - fb r_x joins the
+                                //    list of the LT best (the best of k groups are k
+                                //    distinct rows; a group whose bound on h is under thr
+                                //    holds no g the list keeps), and the threshold tightens;
                                 // 2: the rows whose h = s + fb r_x reaches it are appended
-                                //    to the band (the list's own k best are among them:
-                                //    their h is at least their g).
+                                //    to the band (the rows behind the list's k best among
+                                //    them: their h is at least their g), and their g raise
+                                //    their classes' bests.
     #pragma unroll 1
                                 for (int g = 0; g < kCG; ++g) {
                                     if (__any_sync(0xffffffffu, gm[0] >= thr)) {
                                         const int lcg = c0 + 8 * g - half * kHalfCols;   // in the half
                                         const int64_t row0g = tile_row0 + c0 + 8 * g;
                                         if (gm[0] >= thr) {
+                                            float gbest = -INFINITY;
     #pragma unroll
                                             for (int i = 0; i < 8; ++i) {
                                                 const int64_t row = row0g + i;
                                                 if (row < w.row_end && (int)(row - w.p.row0) != excl)
-                                                    st.offer(fmaf(-fb, wrx[ew][lcg + i], v[i] * sq), 0, 1, 0, -1);
+                                                    gbest = fmaxf(gbest, fmaf(-fb, wrx[ew][lcg + i], v[i] * sq));
                                             }
+                                            st.offer(gbest, 0, 1, 0, -1);
+                                            thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa
+                                                                        : -INFINITY,
+                                                        shared_h);
                                         }
-                                        thr = fmaxf(st.cnt >= w.p.k ? st.kth_score(w.p.k) - 2.0f * fa
-                                                                    : -INFINITY,
-                                                    shared_h);
                                         uint32_t bits = 0;
     #pragma unroll
                                         for (int i = 0; i < 8; ++i) {
