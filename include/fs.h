@@ -76,6 +76,7 @@ typedef struct {
     uint64_t fp64_evals;        /* (query, row) pairs scored in binary64 */
     uint64_t near_ties;         /* binary64 evaluations beyond k (near ties) */
     uint64_t rerank_evals;      /* (query, row) pairs rescored in FP32 */
+    uint64_t band_rows;         /* FP8: rows the scan kept in the queries' bands */
 } fs_stats;
 
 /*

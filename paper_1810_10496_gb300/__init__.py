@@ -28,7 +28,8 @@ FS_MAX_K = 16
 FS_NOALLOC_SCRATCH_BYTES = 32 << 20
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA",
                 4: "FS_ETIMEOUT", 5: "FS_EUNSUPPORTED"}
-STAT_FIELDS = ("queries", "certified", "fallback", "fp64_evals", "near_ties", "rerank_evals")
+STAT_FIELDS = ("queries", "certified", "fallback", "fp64_evals", "near_ties", "rerank_evals",
+               "band_rows")
 STAGES = ("prepare", "scan", "select", "fallback", "gather")
 
 

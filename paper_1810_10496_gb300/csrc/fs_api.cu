@@ -950,6 +950,7 @@ fs_status fs_db_stats(fs_db* db, void* stream, int32_t reset, fs_stats* out) {
     out->fp64_evals = v[kStatFp64];
     out->near_ties = v[kStatNearTies];
     out->rerank_evals = v[kStatRerank];
+    out->band_rows = v[kStatBand];
     return FS_OK;
 }
 

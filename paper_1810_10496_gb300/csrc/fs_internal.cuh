@@ -36,7 +36,7 @@ constexpr uint32_t kStBadSequence = 8u;    // malformed phase-order CSR
 
 // statistics slots (fs_db::stats), same order as fs_stats
 enum { kStatQueries = 0, kStatCertified, kStatFallback, kStatFp64, kStatNearTies,
-       kStatRerank, kNumStats };
+       kStatRerank, kStatBand, kNumStats };
 
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) {
     return (a + b - 1) / b;

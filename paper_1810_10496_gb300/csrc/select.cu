@@ -474,6 +474,7 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
                                 int lane, int q, const SegPlan& p, unsigned long long* stats) {
     const int k = p.k;
     const int n = call.band_cnt[q];
+    if (lane == 0) atomicAdd(&stats[kStatBand], (unsigned long long)n);
     if (n > p.band_cap) return -1;   // the band overflowed its buffer
     uint64_t* band = call.band + p.band0 + (int64_t)(q - p.q0) * p.band_cap;
     const double rq = (double)call.q_resid[q];
@@ -483,12 +484,31 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
     // A. k-th best lower bound: each lane keeps its k best (as order-mapped
     //    keys with the entry's index, so equal values stay distinct), then k
     //    rounds of the warp's largest key below the previous one
+    //    (four entries per lane at a time, so their dependent loads, the key
+    //    and then its row's residual, are in flight together)
     RegList<FS_MAX_K> lo;
     lo.reset();
-    for (int e = lane; e < n; e += 32) {
-        const uint64_t key = band[e];
-        const double l = (double)key_score(key) - a - b * (double)db.resid[p.row0 + key_index(key)];
-        lo.offer((float)l == (float)l ? __double2float_rd(l) : -INFINITY, e, n, 0, -1);
+    for (int e0 = 0; e0 < n; e0 += 4 * 32) {
+        uint64_t key[4];
+        float rx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            key[j] = e < n ? band[e] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            rx[j] = e < n ? db.resid[p.row0 + key_index(key[j])] : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            if (e < n) {
+                const double l = (double)key_score(key[j]) - a - b * (double)rx[j];
+                lo.offer((float)l == (float)l ? __double2float_rd(l) : -INFINITY, e, n, 0, -1);
+            }
+        }
     }
     double L = -INFINITY;
     if (n >= k) {
@@ -514,12 +534,36 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
     RegList<FS_MAX_K> top;
     top.reset();
     int nres = 0;
+    uint64_t keys4[4];
+    float rx4[4];
     for (int e0 = 0; e0 < n; e0 += 32) {
         const int e = e0 + lane;
-        uint64_t key = e < n ? band[e] : 0;
+        const int j4 = (e0 >> 5) & 3;
+        if (j4 == 0) {
+            // the keys and residuals of this and the next three rounds, loaded together
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ej = e0 + 32 * j + lane;
+                keys4[j] = ej < n ? band[ej] : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ej = e0 + 32 * j + lane;
+                rx4[j] = ej < n ? db.resid[p.row0 + key_index(keys4[j])] : 0.0f;
+            }
+        }
+        // round j4's key without a run-time register index
+        uint64_t key = keys4[0];
+        float rxe = rx4[0];
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+            if (j == j4) {
+                key = keys4[j];
+                rxe = rx4[j];
+            }
         bool in = false;
         if (e < n) {
-            const double u = (double)key_score(key) + a + b * (double)db.resid[p.row0 + key_index(key)];
+            const double u = (double)key_score(key) + a + b * (double)rxe;
             in = u >= L;
             if (!in) band[e] = 0;
         }
@@ -554,14 +598,22 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
     const float tk = top.kth_score(kk);
     const float wlo = __double2float_ru((double)tk - 2.0 * (double)p.bound_rerank);
     int nw = 0;
-    for (int e0 = 0; e0 < n; e0 += 32) {
-        const int e = e0 + lane;
-        const uint64_t key = e < n ? band[e] : 0;
-        const bool in = key != 0 && key_score(key) >= wlo;
-        const unsigned m = __ballot_sync(kFull, in);
-        const int pos = nw + __popc(m & ((1u << lane) - 1));
-        if (in && pos < kWindow) sh.widx[wid][pos] = key_index(key);
-        nw += __popc(m);
+    for (int e0 = 0; e0 < n; e0 += 4 * 32) {
+        uint64_t kc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            kc[j] = e < n ? band[e] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t key = kc[j];
+            const bool in = key != 0 && key_score(key) >= wlo;
+            const unsigned m = __ballot_sync(kFull, in);
+            const int pos = nw + __popc(m & ((1u << lane) - 1));
+            if (in && pos < kWindow) sh.widx[wid][pos] = key_index(key);
+            nw += __popc(m);
+        }
     }
     __syncwarp();
     if (lane == 0) atomicAdd(&stats[kStatRerank], (unsigned long long)nres);
