@@ -43,6 +43,15 @@ struct Smem {
     float thr[THREADS];           // each list's current threshold (for the skip vote)
 };
 
+// Two floats in one 64-bit register pair (lo: the first) and the two-lane
+// FMA d = a * b + d on such pairs, each lane rounded to nearest.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | (uint64_t)__float_as_uint(lo);
+}
+__device__ __forceinline__ void fma2(uint64_t& d, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 __device__ __forceinline__ int find_plan(const SegPlan* plan, int n_seg, int64_t item) {
     int lo = 0, hi = n_seg - 1;
     while (lo < hi) {
@@ -125,10 +134,18 @@ k_scan_fp32(DbView db, CallView call) {
             const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 
             float acc[8][8];
+            // dot-product metrics: the accumulators in packed pairs (rows 2p, 2p + 1
+            // of the thread's 8), advanced with the two-lane FMA (each lane an
+            // ordinary rounded fused multiply-add, so every score is the same
+            // sequence of FMAs as with scalar instructions, in half the issues)
+            uint64_t acc2[8][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc2[i][j] = 0ull;
+            }
 
             float4 ra0 = q_ok0 ? *reinterpret_cast<const float4*>(qrow0) : z4;
             float4 ra1 = q_ok1 ? *reinterpret_cast<const float4*>(qrow1) : z4;
@@ -174,17 +191,33 @@ k_scan_fp32(DbView db, CallView call) {
                     a[4] = t1.x; a[5] = t1.y; a[6] = t1.z; a[7] = t1.w;
                     b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
                     b[4] = u1.x; b[5] = u1.y; b[6] = u1.z; b[7] = u1.w;
+                    if (METRIC == FS_MANHATTAN) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
+                        for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (METRIC == FS_MANHATTAN)
-                                acc[i][j] += fabsf(a[i] - b[j]);
-                            else
-                                acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                            for (int j = 0; j < 8; ++j) acc[i][j] += fabsf(a[i] - b[j]);
+                    } else {
+                        uint64_t bp[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) bp[j] = pack2(b[2 * j], b[2 * j + 1]);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const uint64_t ap = pack2(a[i], a[i]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) fma2(acc2[i][j], ap, bp[j]);
                         }
+                    }
                 }
                 buf ^= 1;
+            }
+            if (METRIC != FS_MANHATTAN) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc[i][2 * j] = __uint_as_float((uint32_t)acc2[i][j]);
+                        acc[i][2 * j + 1] = __uint_as_float((uint32_t)(acc2[i][j] >> 32));
+                    }
             }
             // the scores of this thread's 8 queries x 8 rows (standardised
             // metrics: minus the row term; a row above a query's magnitude cap
