@@ -134,17 +134,22 @@ k_scan_fp32(DbView db, CallView call) {
             const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 
             float acc[8][8];
-            // dot-product metrics: the accumulators in packed pairs (rows 2p, 2p + 1
-            // of the thread's 8), advanced with the two-lane FMA (each lane an
-            // ordinary rounded fused multiply-add, so every score is the same
-            // sequence of FMAs as with scalar instructions, in half the issues)
-            uint64_t acc2[8][4];
+            // dot-product metrics: the accumulators in packed pairs (queries 2p,
+            // 2p + 1 of the thread's 8, for one of its rows; pairing queries, whose
+            // values arrive as adjacent pairs in each float4, measured faster than
+            // pairing rows), advanced with the two-lane FMA (each lane an ordinary
+            // rounded fused multiply-add, so every score is the same sequence of
+            // FMAs as with scalar instructions, in half the issues)
+            uint64_t acc2[4][8];   // [query pair][row]
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc2[i][j] = 0ull;
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc2[i][j] = 0ull;
             }
 
             float4 ra0 = q_ok0 ? *reinterpret_cast<const float4*>(qrow0) : z4;
@@ -182,29 +187,29 @@ k_scan_fp32(DbView db, CallView call) {
                 }
 #pragma unroll
                 for (int kk = 0; kk < BK; ++kk) {
-                    float a[8], b[8];
-                    const float4 t0 = *reinterpret_cast<const float4*>(&as[kk][ty * 4]);
-                    const float4 t1 = *reinterpret_cast<const float4*>(&as[kk][64 + ty * 4]);
                     const float4 u0 = *reinterpret_cast<const float4*>(&bs[kk][tx * 4]);
                     const float4 u1 = *reinterpret_cast<const float4*>(&bs[kk][64 + tx * 4]);
-                    a[0] = t0.x; a[1] = t0.y; a[2] = t0.z; a[3] = t0.w;
-                    a[4] = t1.x; a[5] = t1.y; a[6] = t1.z; a[7] = t1.w;
-                    b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
-                    b[4] = u1.x; b[5] = u1.y; b[6] = u1.z; b[7] = u1.w;
+                    const float b[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
                     if (METRIC == FS_MANHATTAN) {
+                        const float4 t0 = *reinterpret_cast<const float4*>(&as[kk][ty * 4]);
+                        const float4 t1 = *reinterpret_cast<const float4*>(&as[kk][64 + ty * 4]);
+                        const float a[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
 #pragma unroll
                             for (int j = 0; j < 8; ++j) acc[i][j] += fabsf(a[i] - b[j]);
                     } else {
-                        uint64_t bp[4];
+                        // the query pairs as two 64-bit halves of each 128-bit load (a
+                        // float4 split into scalars measured slower: the compiler then
+                        // issued extra narrower shared loads)
+                        const ulonglong2 A0 = *reinterpret_cast<const ulonglong2*>(&as[kk][ty * 4]);
+                        const ulonglong2 A1 = *reinterpret_cast<const ulonglong2*>(&as[kk][64 + ty * 4]);
+                        const uint64_t ap[4] = {A0.x, A0.y, A1.x, A1.y};
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) bp[j] = pack2(b[2 * j], b[2 * j + 1]);
+                        for (int j = 0; j < 8; ++j) {
+                            const uint64_t bp = pack2(b[j], b[j]);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const uint64_t ap = pack2(a[i], a[i]);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) fma2(acc2[i][j], ap, bp[j]);
+                            for (int i = 0; i < 4; ++i) fma2(acc2[i][j], ap[i], bp);
                         }
                     }
                 }
@@ -212,11 +217,12 @@ k_scan_fp32(DbView db, CallView call) {
             }
             if (METRIC != FS_MANHATTAN) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        acc[i][2 * j] = __uint_as_float((uint32_t)acc2[i][j]);
-                        acc[i][2 * j + 1] = __uint_as_float((uint32_t)(acc2[i][j] >> 32));
+                    for (int j = 0; j < 8; ++j) {
+                        const uint64_t v = acc2[i][j];
+                        acc[2 * i][j] = __uint_as_float((uint32_t)v);
+                        acc[2 * i + 1][j] = __uint_as_float((uint32_t)(v >> 32));
                     }
             }
             // the scores of this thread's 8 queries x 8 rows (standardised
