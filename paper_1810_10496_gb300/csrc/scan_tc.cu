@@ -451,10 +451,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 // FP8: the scales and residual norms of this warp's half of the
                 // tile, loaded before the wait for the accumulator (lane l: the
                 // half's columns l, l + 32, l + 64, l + 96; rows past the data: 0)
-                float pre_s[4], pre_r[4];
+                constexpr int kStage32 = kHalfCols / 32;   // 32-column slices of the half
+                float pre_s[kStage32], pre_r[kStage32];
                 if (FP8) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < kStage32; ++i) {
                         const int64_t r = tile_row0 + half * kHalfCols + 32 * i + lane;
                         const bool in = r < w.row_end;
                         pre_s[i] = in ? db.scale[r] : 0.0f;
@@ -469,7 +470,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     // staged for this warp alone (its previous tile is done: every
                     // lane passed the __syncwarp at its end)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < kStage32; ++i) {
                         wsx[ew][32 * i + lane] = pre_s[i];
                         wrx[ew][32 * i + lane] = pre_r[i];
                         float rmax = pre_r[i];
@@ -484,12 +485,13 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 bool offered = false;   // the list may have changed in this tile
                 // FP8 threshold on h = s + fb r_x (the upper bound minus fa)
                 const float shared_h = shared_s - fa;
-                // The thread's 128 columns in four chunks of 32, software-pipelined
+                // The thread's columns in chunks of 32, software-pipelined
                 // through two register buffers: the next chunk's TMEM load is in
                 // flight while this chunk is filtered, and the accumulator is freed
                 // as soon as the last chunk has landed, before it is filtered.
                 constexpr int kCW = 32, kCG = kCW / 8;
-                static_assert(kHalfCols == 4 * kCW, "four chunks per half tile");
+                constexpr int kChunks = kHalfCols / kCW;
+                static_assert(kHalfCols % (2 * kCW) == 0, "an even number of chunks per half tile");
                 auto release = [&]() {
                     // every TMEM load of this tile has landed (tcgen05.wait::ld)
                     tc_fence_before();
@@ -657,11 +659,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                 if (FP8) {
                     // one buffer (the FP8 filter's own state needs the registers)
 #pragma unroll 1
-                    for (int cc = 0; cc < 4; ++cc) {
+                    for (int cc = 0; cc < kChunks; ++cc) {
                         uint32_t ra[kCW];
                         tmem_ld_32x32b_x32(taddr + half * kHalfCols + cc * kCW, ra);
                         tmem_ld_wait();
-                        if (cc == 3) release();
+                        if (cc == kChunks - 1) release();
                         filter(ra, half * kHalfCols + cc * kCW);
                     }
                 } else {
@@ -669,17 +671,17 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     tmem_ld_32x32b_x32(taddr + half * kHalfCols, ra);
                     tmem_ld_wait();
 #pragma unroll 1
-                    for (int cc = 0; cc < 4; cc += 2) {
+                    for (int cc = 0; cc < kChunks; cc += 2) {
                         const int c0 = half * kHalfCols + cc * kCW;
                         tmem_ld_32x32b_x32(taddr + c0 + kCW, rb);
                         filter(ra, c0);
                         tmem_ld_wait();
-                        if (cc + 2 < 4)
+                        if (cc + 2 < kChunks)
                             tmem_ld_32x32b_x32(taddr + c0 + 2 * kCW, ra);
                         else
                             release();
                         filter(rb, c0 + kCW);
-                        if (cc + 2 < 4) tmem_ld_wait();
+                        if (cc + 2 < kChunks) tmem_ld_wait();
                     }
                 }
                 if (FP8) {
