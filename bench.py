@@ -717,7 +717,7 @@ def run_ours(args):
     # the GPU answers on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # a bounded sample: about 15 s of oracle work on the host cores
-        ncpu = args.cpu_sample if args.cpu_sample else oracle_sample_size(w, 15.0, 8, 128)
+        ncpu = args.cpu_sample if args.cpu_sample else oracle_sample_size(w, 15.0, 8, 1024)
         pick, ores, dt, spairs = oracle_sample(w, ncpu, metric=args.metric)
         step(db, ws, q_d)
         torch.cuda.synchronize()
