@@ -722,19 +722,31 @@ def run_ours(args):
         step(db, ws, q_d)
         torch.cuda.synchronize()
         ig = outs["idx"].cpu().numpy()
+        dg = outs["dist"].cpu().numpy().astype(np.float64)
         sg = outs["seq_out"].cpu().numpy()
         seg_of_q, _, _, kk = segment_arrays(w)
         hits, exact = [], True
+        err_abs, err_rel = 0.0, 0.0
         for q in pick:
             kq = int(kk[seg_of_q[q]])
             i_o, d_o, s_o, l_o = ores[int(q)]
             hits.append(len(set(ig[q, :kq]) & set(i_o[:kq])) / kq)
             exact &= bool(np.array_equal(ig[q, :kq], i_o[:kq]) and np.array_equal(sg[q, :kq], s_o[:kq]))
+            # distance error where the places hold the same rows
+            same = (ig[q, :kq] == i_o[:kq]) & (i_o[:kq] >= 0)
+            if same.any():
+                e = np.abs(dg[q, :kq][same] - np.asarray(d_o[:kq], dtype=np.float64)[same])
+                err_abs = max(err_abs, float(e.max()))
+                den = np.abs(np.asarray(d_o[:kq], dtype=np.float64)[same])
+                nz = den > 0
+                if nz.any():
+                    err_rel = max(err_rel, float((e[nz] / den[nz]).max()))
         line["cpu_baseline"] = {
             "value": spairs / dt, "unit": UNIT, "cores": _NCPU, "kind": "oracle",
             "sample": f"{len(pick)} of {Q:,} queries, each against its whole database",
             "seconds": dt, "queries_per_s": len(pick) / dt,
-            "sample_recall": float(np.mean(hits)), "sample_exact": exact}
+            "sample_recall": float(np.mean(hits)), "sample_exact": exact,
+            "max_dist_err": {"abs": err_abs, "rel": err_rel}}
         line["recall"] = float(np.mean(hits))
     db.close()
     if rank == 0:
