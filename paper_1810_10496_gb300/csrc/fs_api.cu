@@ -188,7 +188,9 @@ Bounds score_bounds(const fs_db* db, double r_xmax) {
     const double e_norm = (2.0 * eta + eta * eta) * (1.0 + th) + th;
     const double U = (1.0 + eta) * (1.0 + u);   // bound on ||u||
     Bounds b;
-    b.rerank = gamma(m + 5) * U * U + e_norm;
+    // the rerank's warp-wide dot products sum per lane the same elements as
+    // the norms with 128-bit loads (m_norm terms), then a 5-level butterfly
+    b.rerank = gamma(m_norm + 5) * U * U + e_norm;
     b.rx = 0.0;
     if (db->prec == FS_FP32) {
         b.scan = (gamma(db->fu) * U * U + e_norm) * 1.25 + 1e-12;

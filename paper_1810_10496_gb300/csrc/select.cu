@@ -135,6 +135,7 @@ __device__ __forceinline__ void write_padding(const CallView& call, int q, int f
 
 constexpr int kSelWarps = 8;
 constexpr int kRescoreRows = 4;   // window rows the FP32 rescoring reads at once
+constexpr int kBandRows = 4;      // band rows the FP32 rescoring reads at once
 // FP32 distances below this are replaced by the binary64 one (near
 // duplicates; above it the FP32 value is within 3e-6 relative)
 constexpr float kExactDist = 4e-3f;
@@ -175,34 +176,44 @@ __device__ double exact_norm2(const float* __restrict__ q, int f) {
     return a;
 }
 
-// FP32 rescoring of kRescoreRows rows (row < 0: none) against the query's
-// unit vector: the cosine u_q . u_x as a warp-wide sum (each lane sums the
-// features lane, lane + 32, ... with FMA, then a butterfly; every lane ends
-// with the same bits), and with DIST also 1/2 |u_q - u_x|^2 the same way. The
-// error of the cosine is within the plan's bound_rerank.
-template <bool DIST>
+// FP32 rescoring of R rows (row < 0: none) against the query's unit vector:
+// the cosine u_q . u_x as a warp-wide sum (each lane sums, with FMA, the four
+// consecutive features of its 128-bit load in every 128-feature block: at
+// most max(fu / 32, 4 ceil(fu / 128)) terms; then a butterfly; every lane
+// ends with the same bits), and with DIST also 1/2 |u_q - u_x|^2 the same way.
+// The error of the cosine is within the plan's bound_rerank.
+template <bool DIST, int R>
 __device__ __forceinline__ void rescore_rows(const DbView& db, const float* __restrict__ qu,
-                                             const int64_t (&row)[kRescoreRows],
-                                             float (&dot)[kRescoreRows],
-                                             float (&dd)[kRescoreRows], int lane) {
+                                             const int64_t (&row)[R], float (&dot)[R],
+                                             float (&dd)[R], int lane) {
 #pragma unroll
-    for (int j = 0; j < kRescoreRows; ++j) {
+    for (int j = 0; j < R; ++j) {
         dot[j] = 0.0f;
         dd[j] = 0.0f;
         if (row[j] >= 0) {
             const float* xu = db.unit + row[j] * (int64_t)db.fu;
-            for (int i = lane; i < db.fu; i += 32) {
-                const float a = qu[i], b = xu[i];
-                dot[j] = fmaf(a, b, dot[j]);
+            for (int i = 4 * lane; i < db.fu; i += 128) {
+                const float4 a = *reinterpret_cast<const float4*>(qu + i);
+                const float4 b = __ldg(reinterpret_cast<const float4*>(xu + i));
+                dot[j] = fmaf(a.x, b.x, dot[j]);
+                dot[j] = fmaf(a.y, b.y, dot[j]);
+                dot[j] = fmaf(a.z, b.z, dot[j]);
+                dot[j] = fmaf(a.w, b.w, dot[j]);
                 if (DIST) {
-                    const float t = a - b;
+                    float t = a.x - b.x;
+                    dd[j] = fmaf(t, t, dd[j]);
+                    t = a.y - b.y;
+                    dd[j] = fmaf(t, t, dd[j]);
+                    t = a.z - b.z;
+                    dd[j] = fmaf(t, t, dd[j]);
+                    t = a.w - b.w;
                     dd[j] = fmaf(t, t, dd[j]);
                 }
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < kRescoreRows; ++j) {
+    for (int j = 0; j < R; ++j) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dot[j] += __shfl_xor_sync(kFull, dot[j], o);
@@ -335,7 +346,7 @@ __device__ int finish_window(const DbView& db, const CallView& call, SelShared& 
 #pragma unroll
         for (int j = 0; j < kRescoreRows; ++j)
             row[j] = w0 + j < nw ? p.row0 + sh.widx[wid][w0 + j] : -1;
-        rescore_rows<true>(db, qu, row, dot, dd, lane);
+        rescore_rows<true, kRescoreRows>(db, qu, row, dot, dd, lane);
 #pragma unroll
         for (int j = 0; j < kRescoreRows; ++j) {
             if (lane == 0 && row[j] >= 0) {
@@ -527,7 +538,7 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
         L = (double)key_score(kth);
     }
 
-    // B. rescoring of every band row whose upper bound reaches L (kRescoreRows
+    // B. rescoring of every band row whose upper bound reaches L (kBandRows
     //    at a time, warp-wide); its key's score becomes the FP32 cosine, the
     //    other keys are cleared. Every lane keeps the same k best scores.
     const float* qu = call.q_unit + (int64_t)q * db.fu;
@@ -570,19 +581,19 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
         unsigned m = __ballot_sync(kFull, in);
         nres += __popc(m);
         while (m != 0) {
-            int64_t row[kRescoreRows];
-            int slot[kRescoreRows];
+            int64_t row[kBandRows];
+            int slot[kBandRows];
 #pragma unroll
-            for (int j = 0; j < kRescoreRows; ++j) {
+            for (int j = 0; j < kBandRows; ++j) {
                 slot[j] = m != 0 ? __ffs(m) - 1 : -1;
                 if (m != 0) m &= m - 1;
                 const uint64_t kj = __shfl_sync(kFull, key, slot[j] < 0 ? 0 : slot[j]);
                 row[j] = slot[j] < 0 ? -1 : p.row0 + key_index(kj);
             }
-            float dot[kRescoreRows], dd[kRescoreRows];
-            rescore_rows<false>(db, qu, row, dot, dd, lane);
+            float dot[kBandRows], dd[kBandRows];
+            rescore_rows<false, kBandRows>(db, qu, row, dot, dd, lane);
 #pragma unroll
-            for (int j = 0; j < kRescoreRows; ++j) {
+            for (int j = 0; j < kBandRows; ++j) {
                 if (slot[j] < 0) continue;
                 const uint32_t li = (uint32_t)(row[j] - p.row0);
                 top.offer(dot[j], li, ~0u, 0, -1);
