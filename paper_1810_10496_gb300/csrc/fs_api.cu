@@ -436,7 +436,7 @@ Layout make_layout(const fs_db* db, int32_t nq, const Plan& pl) {
     L.band = take(sizeof(uint64_t) * (size_t)pl.total_band);
     L.band_cnt = take(sizeof(int32_t) * (db->prec == FS_FP8_E4M3 ? nq : 0));
     L.class_thr = take(sizeof(uint32_t) * (db->prec == FS_FP8_E4M3 ? (size_t)nq * FS_MAX_K : 0));
-    L.counters = take(4 * sizeof(int32_t));
+    L.counters = take(8 * sizeof(int32_t));
     L.fb_list = take(sizeof(int32_t) * nq);
     L.fb2_list = take(sizeof(int32_t) * nq);
     L.cand_fb = take(sizeof(uint64_t) * (size_t)nq * kFbChunks * kListT);
@@ -526,6 +526,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     c.work_counter = c.fb_count + 1;
     c.fb2_count = c.fb_count + 2;
     c.aborted = c.fb_count + 3;
+    c.sel_counter = c.fb_count + 4;
     c.wait_ns = db->wait_ns;
     c.withhold_load = db->withhold_load;
     c.fb_list = (int32_t*)(ws + L.fb_list);
@@ -581,7 +582,7 @@ fs_status search(const fs_db* db, const float* q, int32_t nq, const int32_t* q_s
     }
     {
         StageTimer t(FS_STAGE_SELECT, cs);
-        FS_CUDA(launch_select(v, c, cs));
+        FS_CUDA(launch_select(v, c, db->num_sms, cs));
         t.finish(1);
     }
     {

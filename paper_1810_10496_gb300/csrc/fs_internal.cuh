@@ -197,7 +197,7 @@ struct CallView {
                               // capacity: then the query goes to the exact fallback)
     int32_t* fb_count;        // queries sent to the FP32 rescan (fb_count[1] is the
                               // scan scheduler, fb_count[2] is fb2_count, fb_count[3]
-                              // is `aborted`)
+                              // is `aborted`, fb_count[4] the selection's counter)
     int32_t* fb_list;         // [nq]
     int32_t* fb2_count;       // queries sent on to the binary64 scan
     int32_t* fb2_list;        // [nq]
@@ -205,6 +205,7 @@ struct CallView {
     double* fb_score;         // [nq][kFbChunks][FS_MAX_K]
     int32_t* fb_index;        // [nq][kFbChunks][FS_MAX_K]
     int32_t* work_counter;    // dynamic scan scheduler
+    int32_t* sel_counter;     // the selection's next query (persistent warps)
     int32_t* aborted;         // nonzero once a bounded wait of this call's scan gave up:
                               // its candidate lists are incomplete, so the selection
                               // writes padding instead of reading them
@@ -243,7 +244,7 @@ cudaError_t launch_write_plan(const SegPlan* host_plan, const int32_t* host_q_or
                               SegPlan* dev_plan, int32_t* dev_q_order, int32_t* fb_count,
                               int32_t* work_counter, cudaStream_t st);
 cudaError_t launch_query_plan(const CallView& call, int32_t* q_plan, cudaStream_t st);
-cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st);
+cudaError_t launch_select(const DbView& db, const CallView& call, int num_sms, cudaStream_t st);
 cudaError_t launch_fallback(const DbView& db, const CallView& call, int num_sms,
                             cudaStream_t st);
 cudaError_t launch_gather(const DbView& db, const CallView& call, int16_t* seq_out,

@@ -27,6 +27,9 @@
 //     multiply-add) and reordered by (score desc, index asc). Everything
 //     else is already in its exact place, because its rescored gaps exceed
 //     the error of both neighbours.
+#include <algorithm>
+#include <mutex>
+
 #include "fs_internal.cuh"
 
 namespace fsk {
@@ -52,6 +55,7 @@ __global__ void k_write_plan(PlanChunk chunk, int n, SegPlan* dst, int32_t* dst_
         fb_count[0] = 0;    // queries for the FP32 rescan
         fb_count[2] = 0;    // queries for the binary64 scan
         fb_count[3] = 0;    // the scan has not given up
+        fb_count[4] = 0;    // the selection's next query
         *work_counter = 0;
     }
 }
@@ -632,23 +636,17 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
     return finish_window(db, call, sh, wid, lane, q, p, nw, stats);
 }
 
-// BAND: the FP8 scan's bands (two resident blocks per SM: the band pass
-// keeps two 16-entry lists per lane); else the candidate lists (at most 48
-// registers: five blocks per SM, fewer waves on large batches).
+// Answers query q (whole warp): padding when the scan gave up, the lowest
+// indices for a zero query, else from the candidate lists or (BAND) the FP8
+// band; a query they do not certify goes to the fallbacks.
 template <bool BAND>
-__global__ void __launch_bounds__(kSelWarps * 32, BAND ? 2 : 5)
-k_select(DbView db, CallView call) {
-    __shared__ SelShared sh;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x < kNumStats) sh.stats[threadIdx.x] = 0;
-    __syncthreads();
-    const int q = blockIdx.x * kSelWarps + wid;
-
-    if (q < call.nq && *call.aborted) {
+__device__ __forceinline__ void select_query(const DbView& db, const CallView& call,
+                                             SelShared& sh, int wid, int lane, int q) {
+    if (*call.aborted) {
         // a bounded wait of the scan gave up (FS_ETIMEOUT in the status word):
         // its candidate lists are incomplete, so no answer is given
         write_padding(call, q, 0);
-    } else if (q < call.nq) {
+    } else {
         const SegPlan p = call.plan[call.q_plan[q]];
         const int k = p.k;
         const int64_t out0 = (int64_t)q * call.k_max;
@@ -700,6 +698,36 @@ k_select(DbView db, CallView call) {
                 atomicAdd(&sh.stats[kStatCertified], 1ull);
             }
         }
+    }
+}
+
+// BAND: the FP8 scan's bands (two resident blocks per SM: the band pass
+// keeps two 16-entry lists per lane), answered by persistent warps that each
+// take the next query from the call's counter: a band holds tens to
+// thousands of rows, and with a query per warp the block's quick warps would
+// wait at its final barrier for the slowest (measured: 21.8 -> 16.8 ms on
+// 8,192 queries of 16.7 M rows). Else the candidate lists, a warp per query
+// (at most 48 registers: five blocks per SM, fewer waves on large batches;
+// their work is even, and the counter measured slightly slower there).
+template <bool BAND>
+__global__ void __launch_bounds__(kSelWarps * 32, BAND ? 2 : 5)
+k_select(DbView db, CallView call) {
+    __shared__ SelShared sh;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kNumStats) sh.stats[threadIdx.x] = 0;
+    __syncthreads();
+    if (BAND) {
+        for (;;) {
+            __syncwarp();   // the previous query's reads of sh are done
+            int q = 0;
+            if (lane == 0) q = atomicAdd(call.sel_counter, 1);
+            q = __shfl_sync(kFull, q, 0);
+            if (q >= call.nq) break;
+            select_query<true>(db, call, sh, wid, lane, q);
+        }
+    } else {
+        const int q = blockIdx.x * kSelWarps + wid;
+        if (q < call.nq) select_query<false>(db, call, sh, wid, lane, q);
     }
     __syncthreads();
     if (threadIdx.x < kNumStats && sh.stats[threadIdx.x])
@@ -1009,13 +1037,37 @@ cudaError_t launch_query_plan(const CallView& call, int32_t* q_plan, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_select(const DbView& db, const CallView& call, cudaStream_t st) {
+// Resident blocks per SM of the band selection on the current device (kept
+// per device: occupancy belongs to the device's context).
+static int select_blocks_per_sm() {
+    static std::mutex mu;
+    static int cached[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    std::lock_guard<std::mutex> g(mu);
+    if (dev >= 0 && dev < kMaxDevices && cached[dev] > 0) return cached[dev];
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_select<true>, kSelWarps * 32, 0) !=
+            cudaSuccess ||
+        nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    if (dev >= 0 && dev < kMaxDevices) cached[dev] = nb;
+    return nb;
+}
+
+cudaError_t launch_select(const DbView& db, const CallView& call, int num_sms, cudaStream_t st) {
     if (call.nq == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)ceil_div(call.nq, kSelWarps);
-    if (db.prec == FS_FP8_E4M3 && db.metric == FS_COSINE)
+    const unsigned per_query = (unsigned)ceil_div(call.nq, kSelWarps);
+    if (db.prec == FS_FP8_E4M3 && db.metric == FS_COSINE) {
+        // one resident wave of persistent blocks, or fewer when the queries need fewer
+        const int64_t resident = (int64_t)std::max(1, num_sms) * select_blocks_per_sm();
+        const unsigned grid = (unsigned)std::min<int64_t>(per_query, resident);
         k_select<true><<<grid, kSelWarps * 32, 0, st>>>(db, call);
-    else
-        k_select<false><<<grid, kSelWarps * 32, 0, st>>>(db, call);
+    } else {
+        k_select<false><<<per_query, kSelWarps * 32, 0, st>>>(db, call);
+    }
     return cudaGetLastError();
 }
 
