@@ -76,7 +76,8 @@ typedef struct {
     uint64_t fp64_evals;        /* (query, row) pairs scored in binary64 */
     uint64_t near_ties;         /* binary64 evaluations beyond k (near ties) */
     uint64_t rerank_evals;      /* (query, row) pairs rescored in FP32 */
-    uint64_t band_rows;         /* FP8: rows the scan kept in the queries' bands */
+    uint64_t band_rows;         /* FP8: band slots the scan filled or reserved (rows kept, plus
+                                   the unused slots of each scan thread's last reservation) */
 } fs_stats;
 
 /*

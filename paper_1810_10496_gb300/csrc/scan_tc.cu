@@ -60,6 +60,8 @@ constexpr int kMaxKBlocks = 4;              // 256 BF16 or 512 FP8 features
 constexpr int kAccs = 512 / BN;              // accumulators in tensor memory
 constexpr uint32_t kTmemCols = kAccs * BN;
 constexpr int kItemQ = 4;                   // claimed items handed on, at most
+constexpr int kBandGrab = 16;               // FP8 band slots a thread reserves at once
+static_assert(kBandGrab >= 8, "a reservation holds a whole group of 8 rows");
 
 struct Bars {
     uint64_t full[kMaxStages];
@@ -436,9 +438,13 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             for (int c = 0; c < LT; ++c) cbest[c] = -INFINITY;
             uint32_t cdirty = 0;
             // FP8: this query's band (rows whose upper bound reaches the running
-            // k-th best lower bound), appended through its counter
+            // k-th best lower bound). The thread appends into slots it reserves
+            // kBandGrab at a time from the query's counter, so the returning
+            // atomic is paid once per reservation rather than once per group;
+            // a reservation's unused slots are written as empty keys (0)
             uint64_t* band = nullptr;
             int32_t* band_cnt = nullptr;
+            int res_at = 0, res_end = 0;   // this thread's reserved slots
             if (FP8 && qvalid) {
                 band = call.band + w.p.band0 + ((int64_t)w.qtile * BM + lq) * w.p.band_cap;
                 band_cnt = call.band_cnt + w.qbase + lq;
@@ -587,7 +593,15 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                             bits |= (in ? 1u : 0u) << i;
                                         }
                                         if (bits != 0) {
-                                            int at = atomicAdd(band_cnt, __popc(bits));
+                                            const int need = __popc(bits);
+                                            if (res_end - res_at < need) {
+                                                for (int e = res_at; e < res_end && e < w.p.band_cap; ++e)
+                                                    band[e] = 0;
+                                                res_at = atomicAdd(band_cnt, kBandGrab);
+                                                res_end = res_at + kBandGrab;
+                                            }
+                                            int at = res_at;
+                                            res_at += need;
                                             for (uint32_t b = bits; b != 0; b &= b - 1, ++at) {
                                                 const int i = __ffs(b) - 1;
                                                 // v[i] without a run-time register index
@@ -704,6 +718,10 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                         published = bound;
                     }
                 }
+            }
+            if (FP8 && qvalid) {
+                // the unused slots of the last reservation
+                for (int e = res_at; e < res_end && e < w.p.band_cap; ++e) band[e] = 0;
             }
             if (!FP8 && ok && qvalid) {
                 const int64_t qlocal = (int64_t)w.qtile * BM + lq;

@@ -470,12 +470,19 @@ __device__ int finish_window(const DbView& db, const CallView& call, SelShared& 
     return nout;
 }
 
+// A band entry holds a row: a key other than 0 (0 marks a slot a scan thread
+// reserved and did not fill) whose row lies in the segment.
+__device__ __forceinline__ bool band_entry(uint64_t key, const SegPlan& p) {
+    return key != 0 && (uint32_t)key_index(key) < (uint32_t)p.nrows;
+}
+
 // Answers query q from its FP8 band: the keys (approximate score s, row) of
 // every row whose upper bound s + E_x reached the scan's running k-th best
 // lower bound, E_x = a + b r_x the row's own bound (r_x its residual norm; a
-// and b per query, from the plan). Returns the places written, or -1 when the
-// band does not certify the answer (it overflowed its buffer, or more than
-// kWindow rows lie within the FP32 rescoring's error of the k-th). Whole warp.
+// and b per query, from the plan), among empty slots. Returns the places
+// written, or -1 when the band does not certify the answer (it overflowed its
+// buffer, or more than kWindow rows lie within the FP32 rescoring's error of
+// the k-th). Whole warp.
 //
 //  A. L = the k-th best lower bound s - E_x over the band: k rows have cosine
 //     at least L, so no row with s + E_x < L is among the k nearest. The band
@@ -512,19 +519,18 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
             key[j] = e < n ? band[e] : 0;
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = e0 + 32 * j + lane;
-            rx[j] = e < n ? db.resid[p.row0 + key_index(key[j])] : 0.0f;
-        }
+        for (int j = 0; j < 4; ++j)
+            rx[j] = band_entry(key[j], p) ? db.resid[p.row0 + key_index(key[j])] : 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int e = e0 + 32 * j + lane;
-            if (e < n) {
+            if (band_entry(key[j], p)) {
                 const double l = (double)key_score(key[j]) - a - b * (double)rx[j];
                 lo.offer((float)l == (float)l ? __double2float_rd(l) : -INFINITY, e, n, 0, -1);
             }
         }
     }
+    // (fewer than k entries: no bound, every entry is rescored)
     double L = -INFINITY;
     if (n >= k) {
         uint64_t prev = ~0ull, kth = 0;
@@ -539,7 +545,7 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
             prev = best;
             kth = best;
         }
-        L = (double)key_score(kth);
+        if (kth != 0) L = (double)key_score(kth);
     }
 
     // B. rescoring of every band row whose upper bound reaches L (kBandRows
@@ -562,10 +568,8 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
                 keys4[j] = ej < n ? band[ej] : 0;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ej = e0 + 32 * j + lane;
-                rx4[j] = ej < n ? db.resid[p.row0 + key_index(keys4[j])] : 0.0f;
-            }
+            for (int j = 0; j < 4; ++j)
+                rx4[j] = band_entry(keys4[j], p) ? db.resid[p.row0 + key_index(keys4[j])] : 0.0f;
         }
         // round j4's key without a run-time register index
         uint64_t key = keys4[0];
@@ -578,8 +582,10 @@ __device__ int answer_from_band(const DbView& db, const CallView& call, SelShare
             }
         bool in = false;
         if (e < n) {
-            const double u = (double)key_score(key) + a + b * (double)rxe;
-            in = u >= L;
+            if (band_entry(key, p)) {
+                const double u = (double)key_score(key) + a + b * (double)rxe;
+                in = u >= L;
+            }
             if (!in) band[e] = 0;
         }
         unsigned m = __ballot_sync(kFull, in);
