@@ -286,6 +286,8 @@ constexpr uint32_t kIdescE4m3 = instr_desc(0, 128, 256);
 static_assert(kIdescBf16 == 0x08400490u, "BF16 M=128 N=256 instruction descriptor");
 static_assert(kIdescE4m3 == 0x08400010u, "E4M3 M=128 N=256 instruction descriptor");
 static_assert(sw128_kmajor_desc(0x400) == 0x4000404000010040ull, "SW128 descriptor layout");
+static_assert(sw128_kmajor_desc(0x400) + ((0x37000u - 0x400u) >> 4) == sw128_kmajor_desc(0x37000),
+              "an address offset below 256 KB adds to the descriptor without a carry");
 
 }  // namespace tc
 }  // namespace fsk
