@@ -47,14 +47,14 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # default plan); absent (reported as null) until captured. Source: the
 # matching summary under profiles/.
 TRAFFIC_BYTES = {
-    # a 1,048,576-row cut (594.1 MB per launch) scaled by the rows to the full
+    # a 1,048,576-row cut (594.8 MB per launch) scaled by the rows to the full
     # 16,777,216 rows: profiles/scan_bf16_precision.md
-    ("scan_bf16", "precision", "bf16"): (9.44e9, None),
-    # the first 64 of the 512 databases (651.5 MB per launch) scaled by the rows
+    ("scan_bf16", "precision", "bf16"): (9.45e9, None),
+    # the first 64 of the 512 databases (653.3 MB per launch) scaled by the rows
     # to all 19,138,960: profiles/scan_bf16_batching.md
-    ("scan_bf16", "batching", "bf16"): (5.36e9, {"items_per_block": 1, "list_len": 16}),
-    ("scan_bf16", "fp32_scale", "bf16"): (313.2e6, None),   # profiles/scan_bf16_fp32_scale.md
-    ("scan_fp8", "fp32_scale", "fp8"): (203.3e6, None),     # profiles/scan_fp8_fp32_scale.md
+    ("scan_bf16", "batching", "bf16"): (5.37e9, {"items_per_block": 1, "list_len": 16}),
+    ("scan_bf16", "fp32_scale", "bf16"): (310.1e6, None),   # profiles/scan_bf16_fp32_scale.md
+    ("scan_fp8", "fp32_scale", "fp8"): (203.6e6, None),     # profiles/scan_fp8_fp32_scale.md
     ("scan_fp32", "fp32_scale", "fp32"): (644.2e6, None),   # profiles/scan_fp32_fp32_scale.md
 }
 
