@@ -479,7 +479,7 @@ __device__ __forceinline__ bool band_entry(uint64_t key, const SegPlan& p) {
 // Answers query q from its FP8 band: the keys (approximate score s, row) of
 // every row whose upper bound s + E_x reached the scan's running k-th best
 // lower bound, E_x = a + b r_x the row's own bound (r_x its residual norm; a
-// and b per query, from the plan), among empty slots. Returns the places
+// and b per query, from the plan), with empty slots among them. Returns the places
 // written, or -1 when the band does not certify the answer (it overflowed its
 // buffer, or more than kWindow rows lie within the FP32 rescoring's error of
 // the k-th). Whole warp.
