@@ -213,7 +213,8 @@ struct CallView {
     int32_t withhold_load;    // test aid: every scan block skips its first row-tile load
     uint32_t* shared_thr;     // [nq] per query: a score below which no row can be
                               // among the k nearest (order-mapped bits)
-    uint32_t* class_thr;      // FP8: [nq][FS_MAX_K] per query and row class (row mod k):
+    uint32_t* class_thr;      // FP8: [nq][FS_MAX_K] per query and row class (k classes, a
+                              // fixed hash of the local row):
                               // the best lower bound of a band row of the class
     const int32_t* exclude;   // [nq] or NULL
     int32_t* out_idx;         // [nq][k_max]

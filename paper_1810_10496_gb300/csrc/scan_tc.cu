@@ -441,10 +441,11 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
             // the selection's test would keep
             const float fa = (w.p.bound_scan + w.p.bound_rq * rq) * 1.0001f;
             const float fb = (w.p.bound_rx + rq) * 1.0011f;
-            // FP8: the shared bound is the least of k class slots (rows of class
-            // c = local row mod k): each slot holds the best lower bound of a
-            // band row of its class, so k distinct band rows reach the least of
-            // them (0 = a class without one yet: no bound)
+            // FP8: the shared bound is the least of k class slots (the rows are
+            // split into k classes by a fixed hash of the local row): each slot
+            // holds the best lower bound of a band row of its class, so k distinct
+            // band rows reach the least of them (0 = a class without one yet: no
+            // bound)
             const uint32_t* shared_p =
                 FP8 ? call.class_thr + (int64_t)(w.qbase + lq) * FS_MAX_K : call.shared_thr + w.qbase + lq;
             auto read_shared = [&]() -> uint32_t {
@@ -635,8 +636,12 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                                                 const float sc = vi * sq;
                                                 const uint32_t li = (uint32_t)(row0g + i - w.p.row0);
                                                 if (at < w.p.band_cap) band[at] = make_key(sc, li);
-                                                // the best lower bound of its class
-                                                const int cls = (int)(li % (uint32_t)w.p.k);
+                                                // the best lower bound of its class: a fixed
+                                                // map of rows onto k classes (a multiplicative
+                                                // hash scaled to [0, k), where li % k would
+                                                // divide once per appended row)
+                                                const int cls =
+                                                    (int)__umulhi(li * 0x9E3779B9u, (uint32_t)w.p.k);
                                                 const float gl = fmaf(-fb, wrx[ew][lcg + i], sc);
     #pragma unroll
                                                 for (int c = 0; c < LT; ++c)
