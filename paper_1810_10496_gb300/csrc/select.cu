@@ -723,12 +723,22 @@ k_select(DbView db, CallView call) {
     if (threadIdx.x < kNumStats) sh.stats[threadIdx.x] = 0;
     __syncthreads();
     if (BAND) {
+        // the counter runs three times over the queries: the first pass takes
+        // the bands of at least a quarter of their capacity, the second those
+        // of at least a sixteenth, the third the rest, so the largest bands
+        // start first and do not extend the launch's tail (every query is
+        // answered once)
         for (;;) {
             __syncwarp();   // the previous query's reads of sh are done
-            int q = 0;
-            if (lane == 0) q = atomicAdd(call.sel_counter, 1);
-            q = __shfl_sync(kFull, q, 0);
-            if (q >= call.nq) break;
+            int i = 0;
+            if (lane == 0) i = atomicAdd(call.sel_counter, 1);
+            i = __shfl_sync(kFull, i, 0);
+            if (i >= 3 * call.nq) break;
+            const int pass = i / call.nq, q = i - pass * call.nq;
+            const int n = call.band_cnt[q];
+            const int cap = call.plan[call.q_plan[q]].band_cap;
+            const int cls = n >= cap / 4 ? 0 : n >= cap / 16 ? 1 : 2;
+            if (cls != pass) continue;
             select_query<true>(db, call, sh, wid, lane, q);
         }
     } else {
