@@ -79,3 +79,40 @@ def test_reference_arm_under_torchrun(tmp_path):
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2
     assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_captured_traffic_only_for_the_captured_run():
+    """The bench attaches an ncu-captured DRAM figure only to a run that
+    matches the capture: the whole workload, the cosine and the plan tuning
+    the capture was taken under."""
+    sys.path.insert(0, ROOT)
+    import bench
+    got = bench.captured_traffic("scan_bf16", "precision", "bf16", "cosine", None, True)
+    assert got is not None and got > 0
+    # a cut of the workload, another metric or a tuned plan: no figure
+    assert bench.captured_traffic("scan_bf16", "precision", "bf16", "cosine", None, False) is None
+    assert bench.captured_traffic("scan_bf16", "precision", "bf16", "euclidean", None, True) is None
+    assert bench.captured_traffic("scan_bf16", "precision", "bf16", "cosine",
+                                  {"list_len": 4}, True) is None
+    # the batch was captured under its autotuned plan: only that plan matches
+    tuned = {"items_per_block": 1, "list_len": 16, "l2_share_pct": 0}
+    assert bench.captured_traffic("scan_bf16", "batching", "bf16", "cosine", tuned, True) > 0
+    assert bench.captured_traffic("scan_bf16", "batching", "bf16", "cosine", None, True) is None
+    assert bench.captured_traffic("scan_bf16", "batching", "bf16", "cosine",
+                                  {"items_per_block": 4, "list_len": 16}, True) is None
+    # never captured
+    assert bench.captured_traffic("scan_fp8", "precision", "fp8", "cosine", None, True) is None
+
+
+def test_oracle_sample_is_bounded():
+    """The CPU baseline's sample stays within its bounds whatever the
+    workload's size."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import fsgen
+    w = fsgen.make("tiny_k3")
+    n = bench.oracle_sample_size(w, 15.0, 8, 1024)
+    assert 1 <= n <= w.q
+    # a huge per-query cost still takes the lower bound, capped by the queries
+    big = fsgen.Workload("x", 0, 10**9, 256, 50, [3])
+    assert bench.oracle_sample_size(big, 15.0, 8, 1024) == 8
