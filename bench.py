@@ -54,7 +54,8 @@ TRAFFIC_BYTES = {
     # to all 19,138,960: profiles/scan_bf16_batching.md
     ("scan_bf16", "batching", "bf16"): (5.37e9, {"items_per_block": 1, "list_len": 16}),
     ("scan_bf16", "fp32_scale", "bf16"): (310.1e6, None),   # profiles/scan_bf16_fp32_scale.md
-    ("scan_fp8", "fp32_scale", "fp8"): (202.9e6, None),     # profiles/scan_fp8_fp32_scale.md
+    # (FP8: the scan changed after its capture in profiles/scan_fp8_fp32_scale.md,
+    # 202.9 MB per launch then, so no captured traffic is attached)
     ("scan_fp32", "fp32_scale", "fp32"): (644.2e6, None),   # profiles/scan_fp32_fp32_scale.md
 }
 

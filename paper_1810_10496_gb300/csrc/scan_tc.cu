@@ -542,14 +542,21 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     #pragma unroll
                         for (int j = 0; j < kCW; ++j) v[j] = __uint_as_float(rbuf[j]);
                         if (FP8) {
-                            const float4* s4 = reinterpret_cast<const float4*>(&wsx[ew][c0 - half * kHalfCols]);
+                            // two scores per instruction (mul.rn.f32x2: each lane an
+                            // ordinary rounded multiply, the same bits as a scalar one)
+                            const ulonglong2* s2 =
+                                reinterpret_cast<const ulonglong2*>(&wsx[ew][c0 - half * kHalfCols]);
     #pragma unroll
                             for (int j = 0; j < kCW / 4; ++j) {
-                                const float4 sc4 = s4[j];
-                                v[4 * j] *= sc4.x;
-                                v[4 * j + 1] *= sc4.y;
-                                v[4 * j + 2] *= sc4.z;
-                                v[4 * j + 3] *= sc4.w;
+                                const ulonglong2 sc = s2[j];
+                                uint64_t p0 = ((uint64_t)rbuf[4 * j + 1] << 32) | rbuf[4 * j];
+                                uint64_t p1 = ((uint64_t)rbuf[4 * j + 3] << 32) | rbuf[4 * j + 2];
+                                asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(p0) : "l"(sc.x));
+                                asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(p1) : "l"(sc.y));
+                                v[4 * j] = __uint_as_float((uint32_t)p0);
+                                v[4 * j + 1] = __uint_as_float((uint32_t)(p0 >> 32));
+                                v[4 * j + 2] = __uint_as_float((uint32_t)p1);
+                                v[4 * j + 3] = __uint_as_float((uint32_t)(p1 >> 32));
                             }
                         }
                         float gm[kCG];
