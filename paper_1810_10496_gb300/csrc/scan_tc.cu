@@ -310,8 +310,8 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
     } else if (warp == 1 && (!PAIR || leader)) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t it = 0, tcount = 0, ic = 0;
-            uint32_t s_next = 0, ph_next = 0;   // ring slot and phase of iteration it
+            uint32_t tcount = 0, ic = 0;
+            uint32_t s_next = 0, ph_next = 0;   // ring slot and phase of the next K block
             bool ok = true;
             // Shared-memory descriptors built once and advanced by addition: the
             // start-address field is the byte address / 16 in the low 14 bits, and
@@ -346,7 +346,7 @@ k_scan_tc(DbView db, CallView call, const __grid_constant__ CUtensorMap map_q,
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d = tmem_base + acc * BN;
-                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    for (int kb = 0; kb < kblocks; ++kb) {
                         const uint32_t s = s_next, ph = ph_next;
                         if (++s_next == (uint32_t)stages) {
                             s_next = 0;
